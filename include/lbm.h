@@ -1,0 +1,228 @@
+/*
+ * lbm.h -- C ABI of liblbm, a GB300 (sm_103a) implementation of the
+ * Kataoka-Tsutahara two-dimensional nine-velocity (D2V9) finite-difference
+ * lattice Boltzmann model with the added dissipation term of
+ * Pan, Xu, Zhang & Jiang, "Lattice Boltzmann Approach to High-Speed
+ * Compressible Flows", Int. J. Mod. Phys. C (2007).
+ *
+ * One call of lbm_step advances every interior node by one time step of
+ * Eq. (SEC-VON-11):
+ *   f_i(x, t + dt) = f_i - dt v_ia d_a f_i + dt lambda_i sum_a d_a^2 f_i
+ *                    + (dt / tau) (f_i^eq - f_i),
+ * with the moments of Eqs. (e4), (e5), (e7), the equilibrium of
+ * Eqs. (e16)-(e18), the beta-upwind first derivative of Eqs. (SEC-VON-2a/2b)
+ * and central second derivatives (Sec. 3, after Eq. SEC-VON-11).
+ *
+ * Conventions (all entry points)
+ *  - Non-dimensional units with R = 1, so P = rho T; b = 2 / (gamma - 1).
+ *  - Velocities (Eq. e14): v_0 = 0; v_1..4 = c1 (-1,0), (0,-1), (1,0), (0,1);
+ *    v_5..8 = (c2 / sqrt 2) (-1,-1), (1,-1), (1,1), (-1,1); eta_0 = eta0,
+ *    eta_1..8 = 0 (Eq. e15).  The diagonal pairs are read as c2 (cos, sin).
+ *  - Cell-centred grid, dx = dy: node (ix, iy) sits at ((ix + 1/2) dx,
+ *    (iy + 1/2) dx), 0 <= ix < nx, 0 <= iy < ny.
+ *  - Field arrays (rho, ux, uy, T) are row-major ny x nx (index iy * nx + ix).
+ *    Distribution arrays are 9 x ny x nx (index (i * ny + iy) * nx + ix).
+ *    Their element type is the storage type of the context: double for
+ *    LBM_FP64, float for the FP32 modes.
+ *  - Pointers passed in may be device memory (cudaMalloc, torch CUDA
+ *    tensors) or host memory (pageable or pinned); the library tells them
+ *    apart with cudaPointerGetAttributes and stages host data through a
+ *    buffer it owns.  Device inputs are read in place.  The caller owns every
+ *    pointer it passes; the library never frees caller memory.
+ *  - Work is queued on the context's stream.  Calls that return data to the
+ *    host (lbm_sync, lbm_conservation, host outputs of lbm_moments,
+ *    lbm_get_f, lbm_save) synchronise that stream before returning.
+ *  - Errors: every call returns an lbm_status; nothing is thrown across the
+ *    ABI.  lbm_last_error gives a message for the last failing call.
+ *  - Health flags (sticky, cleared by lbm_init / lbm_set_f / lbm_load) record
+ *    what the kernels saw in the levels they read: LBM_FLAG_NONPHYSICAL
+ *    (rho <= 0 or a non-finite moment at some node) makes the next
+ *    synchronising call return LBM_E_NONPHYSICAL; LBM_FLAG_T_NONPOSITIVE
+ *    (T <= 0 at some node) is informational only: the scheme passes through
+ *    short episodes of T < 0 right behind strong shocks (e.g. the 1000:1 tube
+ *    of Eq. Riemann-2 with the Fig. 10 constants) and recovers.
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum lbm_status {
+    LBM_OK = 0,
+    LBM_E_INVAL = -1,        /* an argument is out of range (message says which) */
+    LBM_E_NOMEM = -2,        /* device or host allocation failed */
+    LBM_E_CUDA = -3,         /* a CUDA runtime call or kernel launch failed */
+    LBM_E_NONPHYSICAL = -4,  /* a level had rho <= 0 or a non-finite moment */
+    LBM_E_TIMEOUT = -5,      /* a bounded device wait gave up */
+    LBM_E_STATE = -6         /* call out of order (e.g. lbm_step before lbm_init) */
+} lbm_status;
+
+/* Bits of lbm_health. */
+enum {
+    LBM_FLAG_NONPHYSICAL = 1,   /* rho <= 0 or NaN / Inf in a moment */
+    LBM_FLAG_TIMEOUT = 2,       /* a bounded device wait gave up */
+    LBM_FLAG_T_NONPOSITIVE = 4  /* T <= 0 at some node (allowed, informational) */
+};
+
+/* Storage and arithmetic precision of a context. */
+typedef enum lbm_precision {
+    LBM_FP64 = 0,      /* f stored and updated in FP64 */
+    LBM_FP32 = 1,      /* f in FP32; T from the internal energy in FP32 */
+    LBM_FP32_T64 = 2,  /* f in FP32; internal energy for T accumulated in FP64 */
+    LBM_FP32_TDF = 3   /* f in FP32; internal energy for T in double-float
+                          (pairs of FP32 with error-free sums and products) */
+} lbm_precision;
+
+/* Boundary kinds.  The paper names the kinds (Sec. 4.2, text of
+ * Eq. Riemann-3) but not how they act on f; the library uses one ghost layer:
+ *   PERIODIC  ghost = the node at the opposite edge (both opposite sides
+ *             must be PERIODIC and unsplit);
+ *   OUTFLOW   zero gradient: ghost = the adjacent interior node;
+ *   DIRICHLET ghost = f^eq of the side's state (rho, ux, uy, T);
+ *   REFLECT   specular wall halfway between ghost and edge node: ghost_i =
+ *             f_m(i) of the adjacent node, m reversing the wall-normal
+ *             velocity component. */
+typedef enum lbm_bc_kind {
+    LBM_BC_PERIODIC = 0,
+    LBM_BC_OUTFLOW = 1,
+    LBM_BC_DIRICHLET = 2,
+    LBM_BC_REFLECT = 3
+} lbm_bc_kind;
+
+enum { LBM_SIDE_LEFT = 0, LBM_SIDE_RIGHT = 1, LBM_SIDE_BOTTOM = 2, LBM_SIDE_TOP = 3 };
+
+/* One side of the rectangle.  The side may switch kind at the along-side
+ * coordinate s(t) = split0 + split_speed * t (x for bottom/top, y for
+ * left/right, cell-centre coordinates): ghost cells whose centre lies below
+ * s(t) use kind_lo / state_lo, the others kind_hi / state_hi.  Use
+ * split0 = +INFINITY for an unsplit side.  t is the time of the level whose
+ * ghosts are filled (step index times dt).  This expresses the
+ * double-Mach-reflection wall start and its moving exact shock position on
+ * the top boundary (Sec. 4.2, Fig. 12). */
+typedef struct lbm_bc {
+    int kind_lo;
+    int kind_hi;
+    double split0;
+    double split_speed;
+    double state_lo[4]; /* (rho, ux, uy, T) for DIRICHLET below the split */
+    double state_hi[4]; /* ... above the split */
+} lbm_bc;
+
+/* DVM constants of Eqs. (e14), (e15): c1, c2 > 0, c1 != c2 (Eqs. e17, e18
+ * divide by c1^2 - c2^2), eta0 > 0. */
+typedef struct lbm_dvm {
+    double c1, c2, eta0;
+} lbm_dvm;
+
+/* Scheme parameters: beta in [0, 1/2] (Eqs. SEC-VON-2a/2b; 0 = first-order
+ * upwind, 1/2 = central) and the dissipation coefficients lambda_i >= 0 of
+ * Eq. (SEC-VON-11) (Eq. SEC-VON-13 suggests c1 dx, c1 dx / 10 (i = 1..4),
+ * 0 (i = 5..8)). */
+typedef struct lbm_dissipation {
+    double beta;
+    double lambda[9];
+} lbm_dissipation;
+
+typedef struct lbm_ctx lbm_ctx;
+
+/* Create a context for an nx x ny grid (nx, ny >= 1).  b > 0, tau > 0,
+ * dt > 0, dx > 0; the collision factor per step is dt / tau (Eq. SEC-VON-1
+ * with dt equal to the Knudsen number, Sec. 2).  bc[4] in LBM_SIDE_* order.
+ * stream: a cudaStream_t (NULL = the legacy default stream) on the current
+ * device, which the context keeps using.  Allocates two distribution buffers
+ * of 9 x (ny + 2) x pitch elements each (pitch >= nx + 8), owned by the
+ * context.  On failure *out is NULL and lbm_last_error(NULL) explains. */
+lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx,
+                      const lbm_dvm* dvm, const lbm_dissipation* diss, const lbm_bc bc[4],
+                      lbm_precision prec, void* stream, lbm_ctx** out);
+
+/* Free everything the context owns (waits for its stream first). NULL is a
+ * no-op. */
+void lbm_destroy(lbm_ctx* ctx);
+
+/* Message of the last failing call on ctx (ctx = NULL: the last failing
+ * lbm_create of this thread).  Never NULL; valid until the next call. */
+const char* lbm_last_error(const lbm_ctx* ctx);
+
+/* Initial condition f_i = f_i^eq(rho, ux, uy, T) (Eqs. e16-e18) at every node,
+ * ghost layer filled for t = 0; the step counter is reset to 0.  Fields are
+ * ny x nx arrays of the storage type; rho > 0 and T > 0 are the caller's
+ * responsibility (a violation shows as LBM_E_NONPHYSICAL later). */
+lbm_status lbm_init(lbm_ctx* ctx, const void* rho, const void* ux, const void* uy,
+                    const void* T);
+
+/* Advance n >= 0 steps of Eq. (SEC-VON-11), asynchronously on the stream.
+ * Each step reads level k, writes level k + 1 into the other buffer and fills
+ * that level's ghost layer for t = (k + 1) dt in the same kernel. */
+lbm_status lbm_step(lbm_ctx* ctx, int n);
+
+/* Macroscopic fields of the current level (Eqs. e4, e5, e7): rho, ux, uy, T
+ * as ny x nx arrays of the storage type.  Any output may be NULL (skipped). */
+lbm_status lbm_moments(lbm_ctx* ctx, void* rho, void* ux, void* uy, void* T);
+
+/* FP64 totals over the interior of the current level: out[0] = sum rho,
+ * out[1] = sum rho ux, out[2] = sum rho uy, out[3] = sum rho (b T + u^2)
+ * (the sums of Eqs. e4, e5, e7).  Deterministic (fixed reduction order).
+ * out is host memory; synchronises. */
+lbm_status lbm_conservation(lbm_ctx* ctx, double out[4]);
+
+/* Wait for the stream; returns LBM_E_NONPHYSICAL / LBM_E_TIMEOUT if the
+ * corresponding health flag is set. */
+lbm_status lbm_sync(lbm_ctx* ctx);
+
+/* Wait for the stream and store the sticky LBM_FLAG_* bits in *flags (host). */
+lbm_status lbm_health(lbm_ctx* ctx, unsigned* flags);
+
+/* Copy the current level's interior distribution (9 x ny x nx, storage type)
+ * to dst / set it from src (then fill the ghost layer for t = step * dt and
+ * set the step counter to `step`). */
+lbm_status lbm_get_f(lbm_ctx* ctx, void* dst);
+lbm_status lbm_set_f(lbm_ctx* ctx, const void* src, long long step);
+
+/* Step index of the current level. */
+long long lbm_step_count(const lbm_ctx* ctx);
+
+/* Checkpoint: lbm_checkpoint_bytes gives the size; lbm_save writes a header
+ * (grid, precision, step) and the interior distribution to buf (host or
+ * device); lbm_load restores it (LBM_E_INVAL if the header does not match
+ * the context). */
+size_t lbm_checkpoint_bytes(const lbm_ctx* ctx);
+lbm_status lbm_save(lbm_ctx* ctx, void* buf, size_t bytes);
+lbm_status lbm_load(lbm_ctx* ctx, const void* buf, size_t bytes);
+
+/* Launch shape of the step kernel. */
+typedef struct lbm_launch {
+    int variant; /* 0: one thread per node, neighbours read through L1/L2;
+                    1: FP32 modes only: CTAs own column strips and march up a
+                    balanced run of rows, rows of all nine planes staged in a
+                    shared-memory ring by bulk asynchronous copies */
+    int tx;      /* variant 1: columns per CTA, 128 or 256 */
+    int ring;    /* variant 1: ring slots, 4 or 6 (4 when tx = 128) */
+    int grid;    /* variant 1: CTAs; 0 = one full wave (SMs x resident CTAs) */
+} lbm_launch;
+
+/* Set / read the launch shape used by lbm_step (LBM_E_INVAL for shapes the
+ * library does not have; variant 1 on an FP64 context is rejected). */
+lbm_status lbm_set_launch(lbm_ctx* ctx, const lbm_launch* launch);
+lbm_status lbm_get_launch(const lbm_ctx* ctx, lbm_launch* launch);
+
+/* Time every available launch shape for `steps` steps each (CUDA events on
+ * the context's stream, after one untimed step), keep the fastest, and
+ * restore the state and step counter the context had before.  Writes the
+ * chosen shape to *best (may be NULL) and the per-step milliseconds of each
+ * candidate to ms[0..n) if ms is not NULL (n = the number of candidates,
+ * at most 8, stored in *n_candidates if not NULL). */
+lbm_status lbm_autotune(lbm_ctx* ctx, int steps, lbm_launch* best, double* ms, int* n_candidates);
+
+/* Version string of the library. */
+const char* lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LBM_H */

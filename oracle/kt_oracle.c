@@ -37,8 +37,8 @@
  *
  * Build: cc -O2 -ffp-contract=off -fPIC -shared [-fopenmp].  FMA contraction
  * is disabled so that the result is the same on every host architecture.
- * Rows are independent within a step, so the optional OpenMP row loop does not
- * change any result.
+ * Nodes are independent within a step, so the optional OpenMP node loop does
+ * not change any result.
  */
 #include <math.h>
 #include <stddef.h>
@@ -289,11 +289,11 @@ long kt_run(const kt_config* c, double* f, double* work, long nsteps, long n0) {
         double t = (double)(n0 + s) * c->dt;
         kt_fill_ghosts(c, a, t);
 #ifdef _OPENMP
-#pragma omp parallel for schedule(static) num_threads(omp_threads)
+#pragma omp parallel for collapse(2) schedule(static) num_threads(omp_threads)
 #endif
         for (int k = 1; k <= c->ny; ++k) {
-            double out[9];
             for (int j = 1; j <= c->nx; ++j) {
+                double out[9];
                 node_update(c, a, k, j, out);
                 for (int i = 0; i < 9; ++i) bnew[at(c, i, k, j)] = out[i];
             }
@@ -319,6 +319,9 @@ long kt_run(const kt_config* c, double* f, double* work, long nsteps, long n0) {
 void kt_step_nodes(const kt_config* c, double* f, long n, const long* nodes, long count,
                    double* out) {
     kt_fill_ghosts(c, f, (double)n * c->dt);
+#ifdef _OPENMP
+#pragma omp parallel for schedule(static) num_threads(omp_threads)
+#endif
     for (long q = 0; q < count; ++q) {
         int kk = (int)(nodes[q] / c->nx), jj = (int)(nodes[q] % c->nx);
         node_update(c, f, kk + 1, jj + 1, out + 9 * q);

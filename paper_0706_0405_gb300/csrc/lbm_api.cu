@@ -1,0 +1,705 @@
+// lbm_api.cu -- the C ABI of liblbm (declared in include/lbm.h): context
+// lifetime, parameter checks, derived constants, buffer management and the
+// calls that queue the kernels on the caller's stream.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <type_traits>
+
+#include "../../include/lbm.h"
+#include "lbm_launch.h"
+
+using namespace lbm;
+
+struct lbm_ctx {
+    int device = 0;
+    int nx = 0, ny = 0, pitch = 0;
+    long long plane = 0;
+    lbm_precision prec = LBM_FP64;
+    size_t esize = 8;
+    double b = 0, tau = 0, dt = 0, dx = 0;
+    lbm_dvm dvm{};
+    lbm_dissipation diss{};
+    lbm_bc bc[4]{};
+    cudaStream_t stream = nullptr;
+    void* f[2] = {nullptr, nullptr};
+    int cur = 0;            // buffer holding the current level
+    long long step = 0;     // step index of the current level
+    bool ready = false;     // lbm_init / lbm_set_f / lbm_load done
+    unsigned* d_status = nullptr;
+    unsigned* h_status = nullptr;
+    double* d_partials = nullptr;
+    double* d_sums = nullptr;
+    double* h_sums = nullptr;
+    void* d_stage = nullptr;
+    size_t stage_bytes = 0;
+    Model<double> md{};
+    Model<float> mf{};
+    Grid<double> gd{};
+    Grid<float> gf{};
+    StepConfig cfg{};
+    std::string err;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+lbm_status fail(lbm_ctx* c, lbm_status s, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (c)
+        c->err = buf;
+    else
+        g_create_err = buf;
+    return s;
+}
+
+lbm_status cuda_fail(lbm_ctx* c, cudaError_t e, const char* what) {
+    return fail(c, e == cudaErrorMemoryAllocation ? LBM_E_NOMEM : LBM_E_CUDA, "%s: %s", what,
+                cudaGetErrorString(e));
+}
+
+#define LBM_CUDA(ctx, call, what)                              \
+    do {                                                       \
+        cudaError_t e_ = (call);                               \
+        if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+    } while (0)
+
+bool is_device_ptr(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// Velocity signs of Eq. (e14) with the diagonals read as c2 (cos, sin).
+constexpr int SGX[9] = {0, -1, 0, 1, 0, -1, 1, 1, -1};
+constexpr int SGY[9] = {0, 0, -1, 0, 1, -1, -1, 1, 1};
+
+// Derived constants of Eqs. (e16)-(e18) and of the folded update weights of
+// Eqs. (SEC-VON-2a/2b, SEC-VON-11), in FP64.
+Model<double> build_model(const lbm_ctx& c) {
+    Model<double> M{};
+    const double c1 = c.dvm.c1, c2 = c.dvm.c2, e0 = c.dvm.eta0, b = c.b;
+    const double c1s = c1 * c1, c2s = c2 * c2, e0s = e0 * e0;
+    M.omega = c.dt / c.tau;
+    M.c1 = c1;
+    M.d = c2 / std::sqrt(2.0);
+    M.c1s = c1s;
+    M.c2s = c2s;
+    M.eta2 = e0s;
+    M.inv_b = 1.0 / b;
+    M.k0 = (b - 2.0) / e0s;
+    const double q1 = 4.0 * (c1s - c2s), q5 = 4.0 * (c2s - c1s);
+    M.a1c = -c2s / q1;
+    M.a1T = ((b - 2.0) * c2s / e0s + 2.0) / q1;
+    M.a1u = (c2s / c1s) / q1;
+    M.a5c = -c1s / q5;
+    M.a5T = ((b - 2.0) * c1s / e0s + 2.0) / q5;
+    M.a5u = (c1s / c2s) / q5;
+    const double d1 = 2.0 * c1s * (c1s - c2s), d5 = 2.0 * c2s * (c2s - c1s);
+    M.b1c = -c2s / d1;
+    M.b1T = (b + 2.0) / d1;
+    M.b1u = 1.0 / d1;
+    M.b5c = -c1s / d5;
+    M.b5T = (b + 2.0) / d5;
+    M.b5u = 1.0 / d5;
+    M.D1 = 1.0 / (2.0 * c1s * c1s);
+    M.D5 = 1.0 / (2.0 * c2s * c2s);
+    const double beta = c.diss.beta, r = c.dt / c.dx;
+    for (int i = 0; i < 9; ++i) {
+        const double mag = i == 0 ? 0.0 : (i <= 4 ? c1 : M.d);
+        const double ax = SGX[i] * mag * r, ay = SGY[i] * mag * r;
+        const double mu = c.diss.lambda[i] * c.dt / (c.dx * c.dx);
+        double C = 1.0 - M.omega - 4.0 * mu, E = mu, Wt = mu, N = mu, Sd = mu;
+        if (SGX[i] >= 0) {  // Eq. (SEC-VON-2a)
+            E -= ax * beta;
+            C -= ax * (1.0 - 2.0 * beta);
+            Wt += ax * (1.0 - beta);
+        } else {            // Eq. (SEC-VON-2b)
+            E -= ax * (1.0 - beta);
+            C += ax * (1.0 - 2.0 * beta);
+            Wt += ax * beta;
+        }
+        if (SGY[i] >= 0) {
+            N -= ay * beta;
+            C -= ay * (1.0 - 2.0 * beta);
+            Sd += ay * (1.0 - beta);
+        } else {
+            N -= ay * (1.0 - beta);
+            C += ay * (1.0 - 2.0 * beta);
+            Sd += ay * beta;
+        }
+        M.w[i][0] = C;
+        M.w[i][1] = E;
+        M.w[i][2] = Wt;
+        M.w[i][3] = N;
+        M.w[i][4] = Sd;
+    }
+    return M;
+}
+
+void host_equilibrium(const Model<double>& M, double rho, double ux, double uy, double T,
+                      double out[9]) {
+    const double u2 = ux * ux + uy * uy;
+    const double A1 = M.a1c + M.a1T * T + M.a1u * u2, A5 = M.a5c + M.a5T * T + M.a5u * u2;
+    const double B1 = M.b1c + M.b1T * T + M.b1u * u2, B5 = M.b5c + M.b5T * T + M.b5u * u2;
+    out[0] = rho * M.k0 * T;
+    for (int i = 1; i < 9; ++i) {
+        const double mag = i <= 4 ? M.c1 : M.d;
+        const double vu = SGX[i] * mag * ux + SGY[i] * mag * uy;
+        out[i] = i <= 4 ? rho * (A1 + B1 * vu + M.D1 * vu * vu) : rho * (A5 + B5 * vu + M.D5 * vu * vu);
+    }
+}
+
+template <typename S>
+Model<S> cast_model(const Model<double>& d) {
+    Model<S> m;
+    const double* src = reinterpret_cast<const double*>(&d);
+    S* dst = reinterpret_cast<S*>(&m);
+    static_assert(sizeof(Model<double>) / sizeof(double) == sizeof(Model<S>) / sizeof(S), "");
+    for (size_t k = 0; k < sizeof(Model<double>) / sizeof(double); ++k) dst[k] = (S)src[k];
+    return m;
+}
+
+template <typename S>
+Grid<S> build_grid(const lbm_ctx& c, const Model<double>& M) {
+    Grid<S> G{};
+    G.nx = c.nx;
+    G.ny = c.ny;
+    G.pitch = c.pitch;
+    G.plane = c.plane;
+    G.dt = c.dt;
+    G.dx = c.dx;
+    for (int s = 0; s < 4; ++s) {
+        G.kind_lo[s] = c.bc[s].kind_lo;
+        G.kind_hi[s] = c.bc[s].kind_hi;
+        G.split0[s] = c.bc[s].split0;
+        G.split_speed[s] = c.bc[s].split_speed;
+        double lo[9], hi[9];
+        const double* a = c.bc[s].state_lo;
+        const double* b = c.bc[s].state_hi;
+        host_equilibrium(M, a[0], a[1], a[2], a[3], lo);
+        host_equilibrium(M, b[0], b[1], b[2], b[3], hi);
+        for (int i = 0; i < 9; ++i) {
+            G.feq[s][0][i] = (S)lo[i];
+            G.feq[s][1][i] = (S)hi[i];
+        }
+    }
+    return G;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0.0; }
+
+lbm_status validate(int nx, int ny, double b, double tau, double dt, double dx, const lbm_dvm* dvm,
+                    const lbm_dissipation* diss, const lbm_bc* bc, lbm_precision prec) {
+    if (nx < 1 || ny < 1) return fail(nullptr, LBM_E_INVAL, "nx and ny must be >= 1 (got %d, %d)", nx, ny);
+    if (nx > (1 << 24) || ny > (1 << 24)) return fail(nullptr, LBM_E_INVAL, "nx, ny must be <= 2^24");
+    if (!finite_pos(b)) return fail(nullptr, LBM_E_INVAL, "b must be finite and > 0");
+    if (!finite_pos(tau)) return fail(nullptr, LBM_E_INVAL, "tau must be finite and > 0");
+    if (!finite_pos(dt)) return fail(nullptr, LBM_E_INVAL, "dt must be finite and > 0");
+    if (!finite_pos(dx)) return fail(nullptr, LBM_E_INVAL, "dx must be finite and > 0");
+    if (!dvm || !diss || !bc) return fail(nullptr, LBM_E_INVAL, "dvm, diss and bc must not be NULL");
+    if (!finite_pos(dvm->c1) || !finite_pos(dvm->c2) || !finite_pos(dvm->eta0))
+        return fail(nullptr, LBM_E_INVAL, "c1, c2 and eta0 must be finite and > 0");
+    if (dvm->c1 == dvm->c2)
+        return fail(nullptr, LBM_E_INVAL, "c1 == c2 makes the equilibrium singular (Eqs. e17, e18)");
+    if (!(diss->beta >= 0.0 && diss->beta <= 0.5))
+        return fail(nullptr, LBM_E_INVAL, "beta must lie in [0, 0.5] (got %g)", diss->beta);
+    for (int i = 0; i < 9; ++i)
+        if (!(std::isfinite(diss->lambda[i]) && diss->lambda[i] >= 0.0))
+            return fail(nullptr, LBM_E_INVAL, "lambda[%d] must be finite and >= 0", i);
+    if (prec < LBM_FP64 || prec > LBM_FP32_TDF) return fail(nullptr, LBM_E_INVAL, "unknown precision %d", (int)prec);
+    for (int s = 0; s < 4; ++s) {
+        const lbm_bc& q = bc[s];
+        for (int part = 0; part < 2; ++part) {
+            const int k = part ? q.kind_hi : q.kind_lo;
+            if (k < LBM_BC_PERIODIC || k > LBM_BC_REFLECT)
+                return fail(nullptr, LBM_E_INVAL, "side %d: unknown boundary kind %d", s, k);
+            if (k == LBM_BC_DIRICHLET) {
+                const double* st = part ? q.state_hi : q.state_lo;
+                if (!finite_pos(st[0]) || !finite_pos(st[3]) || !std::isfinite(st[1]) || !std::isfinite(st[2]))
+                    return fail(nullptr, LBM_E_INVAL, "side %d: Dirichlet state needs rho > 0, T > 0", s);
+            }
+        }
+        if (std::isnan(q.split0) || !std::isfinite(q.split_speed))
+            return fail(nullptr, LBM_E_INVAL, "side %d: split0 must not be NaN, split_speed finite", s);
+    }
+    for (int s = 0; s < 4; s += 2) {
+        const bool p0 = bc[s].kind_lo == LBM_BC_PERIODIC || bc[s].kind_hi == LBM_BC_PERIODIC;
+        const bool p1 = bc[s + 1].kind_lo == LBM_BC_PERIODIC || bc[s + 1].kind_hi == LBM_BC_PERIODIC;
+        if (p0 || p1) {
+            const bool ok = bc[s].kind_lo == LBM_BC_PERIODIC && bc[s].kind_hi == LBM_BC_PERIODIC &&
+                            bc[s + 1].kind_lo == LBM_BC_PERIODIC && bc[s + 1].kind_hi == LBM_BC_PERIODIC;
+            if (!ok)
+                return fail(nullptr, LBM_E_INVAL, "periodic sides must come in unsplit opposite pairs");
+        }
+    }
+    return LBM_OK;
+}
+
+lbm_status ensure_stage(lbm_ctx* c, size_t bytes) {
+    if (c->stage_bytes >= bytes) return LBM_OK;
+    if (c->d_stage) cudaFree(c->d_stage);
+    c->d_stage = nullptr;
+    c->stage_bytes = 0;
+    LBM_CUDA(c, cudaMalloc(&c->d_stage, bytes), "allocating the staging buffer");
+    c->stage_bytes = bytes;
+    return LBM_OK;
+}
+
+lbm_status read_status(lbm_ctx* c) {
+    LBM_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
+             "reading the status word");
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream), "synchronising the stream");
+    if (*c->h_status & ST_TIMEOUT) return fail(c, LBM_E_TIMEOUT, "a bounded device wait gave up");
+    if (*c->h_status & ST_NONPHYSICAL)
+        return fail(c, LBM_E_NONPHYSICAL, "a level had rho <= 0 or a non-finite moment at some node");
+    return LBM_OK;
+}
+
+lbm_status enter(lbm_ctx* c) {
+    if (!c) return fail(nullptr, LBM_E_INVAL, "NULL context");
+    LBM_CUDA(c, cudaSetDevice(c->device), "selecting the context's device");
+    return LBM_OK;
+}
+
+size_t nodes(const lbm_ctx* c) { return (size_t)c->nx * (size_t)c->ny; }
+
+// Typed dispatch on the storage precision / temperature mode.
+template <typename F>
+cudaError_t dispatch(lbm_ctx* c, F&& fn) {
+    switch (c->prec) {
+    case LBM_FP64: return fn(double{}, std::integral_constant<int, T_PLAIN>{});
+    case LBM_FP32: return fn(float{}, std::integral_constant<int, T_INT32>{});
+    case LBM_FP32_T64: return fn(float{}, std::integral_constant<int, T_INT64>{});
+    default: return fn(float{}, std::integral_constant<int, T_DF>{});
+    }
+}
+
+template <typename S> const Model<S>& model_of(const lbm_ctx* c);
+template <> const Model<double>& model_of<double>(const lbm_ctx* c) { return c->md; }
+template <> const Model<float>& model_of<float>(const lbm_ctx* c) { return c->mf; }
+template <typename S> const Grid<S>& grid_of(const lbm_ctx* c);
+template <> const Grid<double>& grid_of<double>(const lbm_ctx* c) { return c->gd; }
+template <> const Grid<float>& grid_of<float>(const lbm_ctx* c) { return c->gf; }
+
+// Copy `bytes` from a host or device pointer into the staging buffer at
+// `offset` (returns a device pointer to read from), or pass device pointers
+// through.
+lbm_status device_view(lbm_ctx* c, const void* p, size_t bytes, size_t offset, const void** out) {
+    if (p == nullptr) {
+        *out = nullptr;
+        return LBM_OK;
+    }
+    if (is_device_ptr(p)) {
+        *out = p;
+        return LBM_OK;
+    }
+    char* dst = static_cast<char*>(c->d_stage) + offset;
+    LBM_CUDA(c, cudaMemcpyAsync(dst, p, bytes, cudaMemcpyHostToDevice, c->stream), "copying host input");
+    *out = dst;
+    return LBM_OK;
+}
+
+struct CkptHeader {
+    char magic[8];
+    int nx, ny, prec, esize;
+    long long step;
+    long long payload;
+    char pad[24];
+};
+static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
+
+}  // namespace
+
+extern "C" {
+
+const char* lbm_version(void) { return "liblbm 0.1 (KT D2V9 FD-LB with dissipation, sm_103a)"; }
+
+const char* lbm_last_error(const lbm_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_create_err.c_str();
+}
+
+lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx, const lbm_dvm* dvm,
+                      const lbm_dissipation* diss, const lbm_bc bc[4], lbm_precision prec,
+                      void* stream, lbm_ctx** out) {
+    if (!out) return fail(nullptr, LBM_E_INVAL, "out must not be NULL");
+    *out = nullptr;
+    lbm_status s = validate(nx, ny, b, tau, dt, dx, dvm, diss, bc, prec);
+    if (s != LBM_OK) return s;
+    lbm_ctx* c = new lbm_ctx();
+    if (cudaGetDevice(&c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        return fail(nullptr, LBM_E_CUDA, "no CUDA device available");
+    }
+    c->nx = nx;
+    c->ny = ny;
+    c->pitch = ((nx + 2 * PADX) + 31) / 32 * 32;
+    c->plane = (long long)(ny + 2) * c->pitch;
+    c->prec = prec;
+    c->esize = prec == LBM_FP64 ? 8 : 4;
+    c->b = b;
+    c->tau = tau;
+    c->dt = dt;
+    c->dx = dx;
+    c->dvm = *dvm;
+    c->diss = *diss;
+    for (int k = 0; k < 4; ++k) c->bc[k] = bc[k];
+    c->stream = static_cast<cudaStream_t>(stream);
+    if (prec == LBM_FP64) c->cfg.variant = STEP_SIMPLE;
+    c->md = build_model(*c);
+    c->mf = cast_model<float>(c->md);
+    c->gd = build_grid<double>(*c, c->md);
+    c->gf = build_grid<float>(*c, c->md);
+    const size_t fbytes = (size_t)9 * (size_t)c->plane * c->esize;
+    cudaError_t e = cudaSuccess;
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&c->f[k], fbytes);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_status, sizeof(unsigned));
+    const int np = c->prec == LBM_FP64 ? conservation_partials(c->gd) : conservation_partials(c->gf);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_partials, sizeof(double) * 4 * np);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_sums, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_sums, sizeof(double) * 4);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, fbytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->f[1], 0, fbytes, c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    if (e != cudaSuccess) {
+        lbm_status r = cuda_fail(nullptr, e, "allocating context buffers");
+        lbm_destroy(c);
+        return r;
+    }
+    *out = c;
+    return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx* c) {
+    if (!c) return;
+    cudaSetDevice(c->device);
+    cudaStreamSynchronize(c->stream);
+    cudaFree(c->f[0]);
+    cudaFree(c->f[1]);
+    cudaFree(c->d_status);
+    cudaFreeHost(c->h_status);
+    cudaFree(c->d_partials);
+    cudaFree(c->d_sums);
+    cudaFreeHost(c->h_sums);
+    cudaFree(c->d_stage);
+    cudaGetLastError();
+    delete c;
+}
+
+lbm_status lbm_init(lbm_ctx* c, const void* rho, const void* ux, const void* uy, const void* T) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!rho || !ux || !uy || !T) return fail(c, LBM_E_INVAL, "lbm_init: fields must not be NULL");
+    const size_t fb = nodes(c) * c->esize;
+    if ((s = ensure_stage(c, 9 * fb)) != LBM_OK) return s;
+    const void* d[4];
+    const void* in[4] = {rho, ux, uy, T};
+    for (int k = 0; k < 4; ++k)
+        if ((s = device_view(c, in[k], fb, k * fb, &d[k])) != LBM_OK) return s;
+    c->cur = 0;
+    c->step = 0;
+    LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "clearing status");
+    cudaError_t e = dispatch(c, [&](auto tag, auto) {
+        using S = decltype(tag);
+        S* f = static_cast<S*>(c->f[c->cur]);
+        cudaError_t r = launch_init<S>(f, (const S*)d[0], (const S*)d[1], (const S*)d[2], (const S*)d[3],
+                                       model_of<S>(c), grid_of<S>(c), c->stream);
+        if (r == cudaSuccess) r = launch_fill_ghosts<S>(f, grid_of<S>(c), 0, c->stream);
+        return r;
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_init");
+    c->ready = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_step(lbm_ctx* c, int n) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (n < 0) return fail(c, LBM_E_INVAL, "lbm_step: n must be >= 0");
+    if (!c->ready) return fail(c, LBM_E_STATE, "lbm_step before lbm_init / lbm_set_f / lbm_load");
+    for (int k = 0; k < n; ++k) {
+        cudaError_t e = dispatch(c, [&](auto tag, auto tm) {
+            using S = decltype(tag);
+            constexpr int TM = decltype(tm)::value;
+            return launch_step<S, TM>(static_cast<const S*>(c->f[c->cur]), static_cast<S*>(c->f[c->cur ^ 1]),
+                                      model_of<S>(c), grid_of<S>(c), c->step, c->d_status, c->stream, c->cfg);
+        });
+        if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step");
+        c->cur ^= 1;
+        c->step += 1;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_moments(lbm_ctx* c, void* rho, void* ux, void* uy, void* T) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!c->ready) return fail(c, LBM_E_STATE, "lbm_moments before lbm_init");
+    const size_t fb = nodes(c) * c->esize;
+    void* out[4] = {rho, ux, uy, T};
+    void* dev[4];
+    bool host_any = false;
+    for (int k = 0; k < 4; ++k) {
+        if (out[k] && !is_device_ptr(out[k])) host_any = true;
+    }
+    if (host_any && (s = ensure_stage(c, 9 * fb)) != LBM_OK) return s;
+    for (int k = 0; k < 4; ++k)
+        dev[k] = !out[k] ? nullptr : is_device_ptr(out[k]) ? out[k] : static_cast<char*>(c->d_stage) + k * fb;
+    cudaError_t e = dispatch(c, [&](auto tag, auto tm) {
+        using S = decltype(tag);
+        constexpr int TM = decltype(tm)::value;
+        return launch_moments<S, TM>(static_cast<const S*>(c->f[c->cur]), (S*)dev[0], (S*)dev[1], (S*)dev[2],
+                                     (S*)dev[3], model_of<S>(c), grid_of<S>(c), c->d_status, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_moments");
+    for (int k = 0; k < 4; ++k)
+        if (out[k] && dev[k] != out[k])
+            LBM_CUDA(c, cudaMemcpyAsync(out[k], dev[k], fb, cudaMemcpyDeviceToHost, c->stream), "copying moments out");
+    if (host_any) return read_status(c);
+    return LBM_OK;
+}
+
+lbm_status lbm_conservation(lbm_ctx* c, double out[4]) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!out) return fail(c, LBM_E_INVAL, "lbm_conservation: out must not be NULL");
+    if (!c->ready) return fail(c, LBM_E_STATE, "lbm_conservation before lbm_init");
+    cudaError_t e = dispatch(c, [&](auto tag, auto) {
+        using S = decltype(tag);
+        return launch_conservation<S>(static_cast<const S*>(c->f[c->cur]), c->md, grid_of<S>(c), c->d_partials,
+                                      c->d_sums, c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_conservation");
+    LBM_CUDA(c, cudaMemcpyAsync(c->h_sums, c->d_sums, 4 * sizeof(double), cudaMemcpyDeviceToHost, c->stream),
+             "copying sums");
+    s = read_status(c);
+    for (int k = 0; k < 4; ++k) out[k] = c->h_sums[k];
+    return s;
+}
+
+lbm_status lbm_sync(lbm_ctx* c) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    return read_status(c);
+}
+
+lbm_status lbm_health(lbm_ctx* c, unsigned* flags) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!flags) return fail(c, LBM_E_INVAL, "lbm_health: flags must not be NULL");
+    LBM_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
+             "reading the status word");
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream), "synchronising the stream");
+    *flags = *c->h_status;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_f(lbm_ctx* c, void* dst) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!dst) return fail(c, LBM_E_INVAL, "lbm_get_f: dst must not be NULL");
+    if (!c->ready) return fail(c, LBM_E_STATE, "lbm_get_f before lbm_init");
+    const size_t bytes = 9 * nodes(c) * c->esize;
+    const bool dev = is_device_ptr(dst);
+    if (!dev && (s = ensure_stage(c, bytes)) != LBM_OK) return s;
+    void* target = dev ? dst : c->d_stage;
+    cudaError_t e = dispatch(c, [&](auto tag, auto) {
+        using S = decltype(tag);
+        return launch_pack<S>(static_cast<const S*>(c->f[c->cur]), (S*)target, grid_of<S>(c), c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_get_f");
+    if (!dev) {
+        LBM_CUDA(c, cudaMemcpyAsync(dst, c->d_stage, bytes, cudaMemcpyDeviceToHost, c->stream), "copying f out");
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream), "synchronising the stream");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_set_f(lbm_ctx* c, const void* src, long long step) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!src) return fail(c, LBM_E_INVAL, "lbm_set_f: src must not be NULL");
+    if (step < 0) return fail(c, LBM_E_INVAL, "lbm_set_f: step must be >= 0");
+    const size_t bytes = 9 * nodes(c) * c->esize;
+    if (!is_device_ptr(src) && (s = ensure_stage(c, bytes)) != LBM_OK) return s;
+    const void* d;
+    if ((s = device_view(c, src, bytes, 0, &d)) != LBM_OK) return s;
+    LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "clearing status");
+    cudaError_t e = dispatch(c, [&](auto tag, auto) {
+        using S = decltype(tag);
+        S* f = static_cast<S*>(c->f[c->cur]);
+        cudaError_t r = launch_unpack<S>(f, (const S*)d, grid_of<S>(c), c->stream);
+        if (r == cudaSuccess) r = launch_fill_ghosts<S>(f, grid_of<S>(c), step, c->stream);
+        return r;
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_f");
+    c->step = step;
+    c->ready = true;
+    return LBM_OK;
+}
+
+long long lbm_step_count(const lbm_ctx* c) { return c ? c->step : -1; }
+
+lbm_status lbm_set_launch(lbm_ctx* c, const lbm_launch* l) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!l) return fail(c, LBM_E_INVAL, "lbm_set_launch: launch must not be NULL");
+    if (l->variant != STEP_SIMPLE && l->variant != STEP_RING)
+        return fail(c, LBM_E_INVAL, "lbm_set_launch: unknown variant %d", l->variant);
+    if (l->variant == STEP_RING) {
+        if (c->prec == LBM_FP64) return fail(c, LBM_E_INVAL, "lbm_set_launch: variant 1 is FP32-only");
+        const bool ok = (l->tx == 256 && (l->ring == 4 || l->ring == 6)) || (l->tx == 128 && l->ring == 4);
+        if (!ok) return fail(c, LBM_E_INVAL, "lbm_set_launch: tx/ring must be 256/4, 256/6 or 128/4");
+        if (l->grid < 0) return fail(c, LBM_E_INVAL, "lbm_set_launch: grid must be >= 0");
+    }
+    c->cfg.variant = l->variant;
+    c->cfg.tx = l->tx;
+    c->cfg.ring = l->ring;
+    c->cfg.grid = l->grid;
+    return LBM_OK;
+}
+
+lbm_status lbm_get_launch(const lbm_ctx* c, lbm_launch* l) {
+    if (!c || !l) return fail(nullptr, LBM_E_INVAL, "lbm_get_launch: NULL argument");
+    l->variant = c->cfg.variant;
+    l->tx = c->cfg.tx;
+    l->ring = c->cfg.ring;
+    l->grid = c->cfg.grid;
+    return LBM_OK;
+}
+
+lbm_status lbm_autotune(lbm_ctx* c, int steps, lbm_launch* best, double* ms, int* n_candidates) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (steps < 1) return fail(c, LBM_E_INVAL, "lbm_autotune: steps must be >= 1");
+    if (!c->ready) return fail(c, LBM_E_STATE, "lbm_autotune before lbm_init");
+    lbm_launch cands[8];
+    int nc = 0;
+    cands[nc++] = {STEP_SIMPLE, 0, 0, 0};
+    if (c->prec != LBM_FP64) {
+        cands[nc++] = {STEP_RING, 256, 4, 0};
+        cands[nc++] = {STEP_RING, 256, 6, 0};
+        cands[nc++] = {STEP_RING, 128, 4, 0};
+    }
+    // save the state (interior via the staging buffer, step counter, flags)
+    const size_t bytes = 9 * nodes(c) * c->esize;
+    if ((s = ensure_stage(c, bytes)) != LBM_OK) return s;
+    const long long step0 = c->step;
+    const StepConfig cfg0 = c->cfg;
+    cudaError_t e = dispatch(c, [&](auto tag, auto) {
+        using S = decltype(tag);
+        return launch_pack<S>(static_cast<const S*>(c->f[c->cur]), (S*)c->d_stage, grid_of<S>(c), c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_autotune: saving the state");
+    LBM_CUDA(c, cudaMemcpyAsync(c->h_status, c->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, c->stream),
+             "lbm_autotune: saving the flags");
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream), "lbm_autotune");
+    const unsigned flags0 = *c->h_status;
+    cudaEvent_t ev[2];
+    LBM_CUDA(c, cudaEventCreate(&ev[0]), "lbm_autotune: events");
+    LBM_CUDA(c, cudaEventCreate(&ev[1]), "lbm_autotune: events");
+    int bi = -1;
+    float bt = 0.0f;
+    lbm_status r = LBM_OK;
+    for (int k = 0; k < nc && r == LBM_OK; ++k) {
+        c->cfg = StepConfig{cands[k].variant, cands[k].tx, cands[k].ring, cands[k].grid};
+        if ((r = lbm_step(c, 1)) != LBM_OK) break;
+        cudaEventRecord(ev[0], c->stream);
+        if ((r = lbm_step(c, steps)) != LBM_OK) break;
+        cudaEventRecord(ev[1], c->stream);
+        if (cudaEventSynchronize(ev[1]) != cudaSuccess) {
+            r = fail(c, LBM_E_CUDA, "lbm_autotune: timing failed");
+            break;
+        }
+        float t = 0.0f;
+        cudaEventElapsedTime(&t, ev[0], ev[1]);
+        if (ms) ms[k] = t / steps;
+        if (bi < 0 || t < bt) {
+            bi = k;
+            bt = t;
+        }
+    }
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+    // restore the state whatever happened
+    e = dispatch(c, [&](auto tag, auto) {
+        using S = decltype(tag);
+        S* f = static_cast<S*>(c->f[c->cur]);
+        cudaError_t q = launch_unpack<S>(f, (const S*)c->d_stage, grid_of<S>(c), c->stream);
+        if (q == cudaSuccess) q = launch_fill_ghosts<S>(f, grid_of<S>(c), step0, c->stream);
+        return q;
+    });
+    c->step = step0;
+    *c->h_status = flags0;
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(c->d_status, c->h_status, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_autotune: restoring the state");
+    if (r != LBM_OK) {
+        c->cfg = cfg0;
+        return r;
+    }
+    c->cfg = StepConfig{cands[bi].variant, cands[bi].tx, cands[bi].ring, cands[bi].grid};
+    if (best) *best = cands[bi];
+    if (n_candidates) *n_candidates = nc;
+    return LBM_OK;
+}
+
+size_t lbm_checkpoint_bytes(const lbm_ctx* c) {
+    return c ? sizeof(CkptHeader) + 9 * nodes(c) * c->esize : 0;
+}
+
+lbm_status lbm_save(lbm_ctx* c, void* buf, size_t bytes) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!buf || bytes < lbm_checkpoint_bytes(c))
+        return fail(c, LBM_E_INVAL, "lbm_save: buffer must hold lbm_checkpoint_bytes() bytes");
+    if (!c->ready) return fail(c, LBM_E_STATE, "lbm_save before lbm_init");
+    CkptHeader h{};
+    std::memcpy(h.magic, "KTLBMCK1", 8);
+    h.nx = c->nx;
+    h.ny = c->ny;
+    h.prec = (int)c->prec;
+    h.esize = (int)c->esize;
+    h.step = c->step;
+    h.payload = (long long)(9 * nodes(c) * c->esize);
+    char* p = static_cast<char*>(buf);
+    if (is_device_ptr(buf)) {
+        LBM_CUDA(c, cudaMemcpyAsync(p, &h, sizeof h, cudaMemcpyHostToDevice, c->stream), "writing header");
+        if ((s = lbm_get_f(c, p + sizeof h)) != LBM_OK) return s;
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream), "synchronising the stream");
+        return LBM_OK;
+    }
+    std::memcpy(p, &h, sizeof h);
+    return lbm_get_f(c, p + sizeof h);
+}
+
+lbm_status lbm_load(lbm_ctx* c, const void* buf, size_t bytes) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!buf || bytes < sizeof(CkptHeader)) return fail(c, LBM_E_INVAL, "lbm_load: buffer too small");
+    CkptHeader h{};
+    const char* p = static_cast<const char*>(buf);
+    if (is_device_ptr(buf))
+        LBM_CUDA(c, cudaMemcpy(&h, p, sizeof h, cudaMemcpyDeviceToHost), "reading header");
+    else
+        std::memcpy(&h, p, sizeof h);
+    if (std::memcmp(h.magic, "KTLBMCK1", 8) != 0 || h.nx != c->nx || h.ny != c->ny || h.prec != (int)c->prec ||
+        h.payload != (long long)(9 * nodes(c) * c->esize) || bytes < lbm_checkpoint_bytes(c) || h.step < 0)
+        return fail(c, LBM_E_INVAL, "lbm_load: checkpoint does not match this context");
+    return lbm_set_f(c, p + sizeof h, h.step);
+}
+
+}  // extern "C"

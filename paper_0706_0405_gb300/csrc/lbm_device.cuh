@@ -1,0 +1,263 @@
+// lbm_device.cuh -- device-side pieces of the KT D2V9 finite-difference
+// lattice Boltzmann step (Pan, Xu, Zhang & Jiang, IJMPC 2007) shared by the
+// kernels of liblbm: the constant block, moments, equilibrium and ghost rules.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace lbm {
+
+// Interior column 0 sits at array column PADX, so that interior rows start on
+// a 32-byte boundary for FP64 and FP32 alike; the ghost columns are PADX - 1
+// and PADX + nx.  Rows 0 and ny + 1 are the ghost rows.
+constexpr int PADX = 4;
+
+// Temperature recovery variants of the FP32 modes (see lbm.h).
+enum TMode : int {
+    T_PLAIN = 0,  // T = (E / rho - u^2) / b in the storage precision (FP64 mode)
+    T_INT32 = 1,  // T = sum f_i |v_i - u|^2 (+ eta^2 on i = 0) / (b rho), FP32
+    T_INT64 = 2,  // same, the nine exact FP32 products summed in FP64
+    T_DF = 3      // same, summed in double-float (error-free FP32 transforms)
+};
+
+enum BcKind : int { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_DIRICHLET = 2, BC_REFLECT = 3 };
+enum Side : int { S_LEFT = 0, S_RIGHT = 1, S_BOTTOM = 2, S_TOP = 3 };
+
+// Per-context constants, rounded once to the storage type on the host.
+// Update of population i at node x (Eq. SEC-VON-11 with the beta-upwind
+// derivative of Eqs. SEC-VON-2a/2b and central second differences folded in):
+//   f_i' = w[i][0] f_i(x) + w[i][1] f_i(x+dx) + w[i][2] f_i(x-dx)
+//        + w[i][3] f_i(y+dy) + w[i][4] f_i(y-dy) + omega f_i^eq(x),
+// where w[i][0] already holds the -omega of the relaxation.
+template <typename S>
+struct Model {
+    S w[9][5];
+    S omega;          // dt / tau
+    S c1, d;          // axis speed c1; diagonal component c2 / sqrt(2)
+    S c1s, c2s, eta2; // c1^2, c2^2, eta0^2
+    S inv_b;          // 1 / b
+    S k0;             // A_0 / T = (b - 2) / eta0^2 (Eq. e17)
+    S a1c, a1T, a1u;  // A_1..4 = a1c + a1T T + a1u u^2 (Eq. e17)
+    S a5c, a5T, a5u;  // A_5..8
+    S b1c, b1T, b1u;  // B_1..4 = b1c + b1T T + b1u u^2 (Eq. e18)
+    S b5c, b5T, b5u;  // B_5..8
+    S D1, D5;         // D_1..4, D_5..8 (Eq. e18)
+};
+
+// Grid and boundary description.
+template <typename S>
+struct Grid {
+    int nx, ny, pitch;
+    long long plane;              // elements per population plane = (ny + 2) * pitch
+    int kind_lo[4], kind_hi[4];
+    double split0[4], split_speed[4];
+    double dt, dx;
+    S feq[4][2][9];               // f^eq of each side's lo / hi Dirichlet state
+};
+
+// Mirror maps of a reflecting wall: reverse v_x (left/right) or v_y
+// (bottom/top) of the velocities of Eq. (e14).
+__host__ __device__ constexpr int mirror_x(int i) {
+    return i == 1 ? 3 : i == 3 ? 1 : i == 5 ? 6 : i == 6 ? 5 : i == 7 ? 8 : i == 8 ? 7 : i;
+}
+__host__ __device__ constexpr int mirror_y(int i) {
+    return i == 2 ? 4 : i == 4 ? 2 : i == 5 ? 8 : i == 8 ? 5 : i == 6 ? 7 : i == 7 ? 6 : i;
+}
+
+// ------------------------------------------------------ explicit rounding
+// Every operation of the node update is written with a round-to-nearest
+// intrinsic, so the compiler cannot contract or reorder it: all kernel
+// variants then produce the same bits for the same level.
+__device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
+__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+__device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
+__device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
+__device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
+__device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
+__device__ __forceinline__ double rcp_(double a) { return __drcp_rn(a); }
+
+// ---------------------------------------------------------------- moments
+// rho = sum f (Eq. e4), rho u = sum f v (Eq. e5), T from Eq. (e7).
+template <typename S, int TM>
+__device__ __forceinline__ void moments(const S (&f)[9], const Model<S>& M, S& rho, S& ux, S& uy,
+                                        S& T) {
+    const S s14 = add_(add_(f[1], f[3]), add_(f[2], f[4]));
+    const S s58 = add_(add_(f[5], f[7]), add_(f[6], f[8]));
+    rho = add_(add_(f[0], s14), s58);
+    const S jx = fma_(M.c1, sub_(f[3], f[1]), mul_(M.d, sub_(add_(f[6], f[7]), add_(f[5], f[8]))));
+    const S jy = fma_(M.c1, sub_(f[4], f[2]), mul_(M.d, sub_(add_(f[7], f[8]), add_(f[5], f[6]))));
+    const S inv = rcp_(rho);
+    ux = mul_(jx, inv);
+    uy = mul_(jy, inv);
+    if constexpr (TM == T_PLAIN) {
+        const S E = fma_(M.eta2, f[0], fma_(M.c1s, s14, mul_(M.c2s, s58)));
+        T = mul_(sub_(mul_(E, inv), fma_(ux, ux, mul_(uy, uy))), M.inv_b);
+    } else {
+        // Internal energy sum_i f_i (|v_i - u|^2 + eta_i^2) = E - rho u^2; its
+        // terms are formed around u, so the large totals never cancel, and an
+        // error in u enters only at second order.
+        const S ux2 = mul_(ux, ux), uy2 = mul_(uy, uy);
+        const S xm = add_(M.c1, ux), xp = sub_(M.c1, ux), ym = add_(M.c1, uy), yp = sub_(M.c1, uy);
+        const S dxm = add_(M.d, ux), dxp = sub_(M.d, ux), dym = add_(M.d, uy), dyp = sub_(M.d, uy);
+        const S qxm = mul_(dxm, dxm), qxp = mul_(dxp, dxp), qym = mul_(dym, dym), qyp = mul_(dyp, dyp);
+        const S w[9] = {add_(M.eta2, add_(ux2, uy2)), fma_(xm, xm, uy2), fma_(ym, ym, ux2),
+                        fma_(xp, xp, uy2),            fma_(yp, yp, ux2), add_(qxm, qym),
+                        add_(qxp, qym),               add_(qxp, qyp),    add_(qxm, qyp)};
+        S e;
+        if constexpr (TM == T_INT32) {
+            e = mul_(f[0], w[0]);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) e = fma_(f[i], w[i], e);
+        } else if constexpr (TM == T_INT64) {
+            double acc = __dmul_rn((double)f[0], (double)w[0]);
+#pragma unroll
+            for (int i = 1; i < 9; ++i) acc = __fma_rn((double)f[i], (double)w[i], acc);
+            e = (S)acc;
+        } else {  // T_DF: exact products p_i + q_i summed by TwoSum (Knuth)
+            float hi = 0.0f, lo = 0.0f;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float p = mul_(f[i], w[i]);
+                const float q = fma_(f[i], w[i], -p);
+                const float s = add_(hi, p);
+                const float bb = sub_(s, hi);
+                lo = add_(lo, add_(add_(sub_(hi, sub_(s, bb)), sub_(p, bb)), q));
+                hi = s;
+            }
+            e = add_(hi, lo);
+        }
+        T = mul_(mul_(e, inv), M.inv_b);
+    }
+}
+
+// Equilibrium of Eqs. (e16)-(e18): f_i^eq = rho (A_i + B_i v.u + D_i (v.u)^2).
+template <typename S>
+__device__ __forceinline__ void equilibrium(const Model<S>& M, S rho, S ux, S uy, S T, S (&fe)[9]) {
+    const S u2 = fma_(ux, ux, mul_(uy, uy));
+    const S A1 = fma_(M.a1u, u2, fma_(M.a1T, T, M.a1c));
+    const S A5 = fma_(M.a5u, u2, fma_(M.a5T, T, M.a5c));
+    const S B1 = fma_(M.b1u, u2, fma_(M.b1T, T, M.b1c));
+    const S B5 = fma_(M.b5u, u2, fma_(M.b5T, T, M.b5c));
+    const S p = mul_(M.c1, ux), q = mul_(M.c1, uy);               // v.u of i = 3, 4 (-: 1, 2)
+    const S r = mul_(M.d, add_(ux, uy)), m = mul_(M.d, sub_(ux, uy));  // v.u of i = 7, 6 (-: 5, 8)
+    fe[0] = mul_(rho, mul_(M.k0, T));
+    const S sp = fma_(mul_(M.D1, p), p, A1), sq = fma_(mul_(M.D1, q), q, A1);
+    const S sr = fma_(mul_(M.D5, r), r, A5), sm = fma_(mul_(M.D5, m), m, A5);
+    fe[1] = mul_(rho, fma_(-B1, p, sp));
+    fe[3] = mul_(rho, fma_(B1, p, sp));
+    fe[2] = mul_(rho, fma_(-B1, q, sq));
+    fe[4] = mul_(rho, fma_(B1, q, sq));
+    fe[5] = mul_(rho, fma_(-B5, r, sr));
+    fe[7] = mul_(rho, fma_(B5, r, sr));
+    fe[6] = mul_(rho, fma_(B5, m, sm));
+    fe[8] = mul_(rho, fma_(-B5, m, sm));
+}
+
+// Update of one population from its five-point star and its equilibrium
+// (Eq. SEC-VON-11 with the folded weights of Model::w).
+template <typename S>
+__device__ __forceinline__ S update(const Model<S>& M, int i, S fe, S c, S e, S w, S n, S s) {
+    S acc = mul_(M.omega, fe);
+    acc = fma_(M.w[i][0], c, acc);
+    acc = fma_(M.w[i][1], e, acc);
+    acc = fma_(M.w[i][2], w, acc);
+    acc = fma_(M.w[i][3], n, acc);
+    return fma_(M.w[i][4], s, acc);
+}
+
+// ---------------------------------------------------------- ghost layer
+// Which part (lo = 0 / hi = 1) of `side` applies at along-side coordinate
+// `along` for time level `level`: lo iff along < split0 + split_speed t with
+// t = level * dt, all in FP64 with explicit rounding so that the decision is
+// the same as a plain IEEE evaluation of that expression on any host.
+template <typename S>
+__device__ __forceinline__ int side_part(const Grid<S>& G, int side, int along_index,
+                                         long long level) {
+    const double t = __dmul_rn((double)level, G.dt);
+    const double split = __dadd_rn(G.split0[side], __dmul_rn(G.split_speed[side], t));
+    const double along = __dmul_rn((double)along_index + 0.5, G.dx);
+    return along < split ? 0 : 1;
+}
+
+template <typename S>
+__device__ __forceinline__ size_t cell(const Grid<S>& G, int ix, int iy) {
+    return (size_t)(iy + 1) * (size_t)G.pitch + (size_t)(ix + PADX);
+}
+
+// Write the ghost cells of level `level` that the edge node (ix, iy), whose
+// nine level values are v, is responsible for: its own side's ghost for
+// OUTFLOW / REFLECT / DIRICHLET, and the opposite side's ghost for PERIODIC.
+template <typename S>
+__device__ __forceinline__ void write_ghosts(const Grid<S>& G, S* __restrict__ f, int ix, int iy,
+                                             const S (&v)[9], long long level) {
+    const size_t pl = (size_t)G.plane;
+    // left / right sides: ghost columns, along-coordinate = iy
+    if (ix == 0 || ix == G.nx - 1) {
+#pragma unroll
+        for (int side = S_LEFT; side <= S_RIGHT; ++side) {
+            const int part = side_part(G, side, iy, level);
+            const int kind = part ? G.kind_hi[side] : G.kind_lo[side];
+            const int own = side == S_LEFT ? 0 : G.nx - 1;
+            const int far = side == S_LEFT ? G.nx - 1 : 0;
+            const size_t gc = (size_t)(iy + 1) * G.pitch + (side == S_LEFT ? PADX - 1 : PADX + G.nx);
+            if (kind == BC_PERIODIC) {
+                if (ix == far)
+                    for (int i = 0; i < 9; ++i) f[i * pl + gc] = v[i];
+            } else if (ix == own) {
+                if (kind == BC_OUTFLOW)
+                    for (int i = 0; i < 9; ++i) f[i * pl + gc] = v[i];
+                else if (kind == BC_REFLECT)
+                    for (int i = 0; i < 9; ++i) f[i * pl + gc] = v[mirror_x(i)];
+                else
+                    for (int i = 0; i < 9; ++i) f[i * pl + gc] = G.feq[side][part][i];
+            }
+        }
+    }
+    if (iy == 0 || iy == G.ny - 1) {
+#pragma unroll
+        for (int side = S_BOTTOM; side <= S_TOP; ++side) {
+            const int part = side_part(G, side, ix, level);
+            const int kind = part ? G.kind_hi[side] : G.kind_lo[side];
+            const int own = side == S_BOTTOM ? 0 : G.ny - 1;
+            const int far = side == S_BOTTOM ? G.ny - 1 : 0;
+            const size_t gc = (size_t)(side == S_BOTTOM ? 0 : G.ny + 1) * G.pitch + (ix + PADX);
+            if (kind == BC_PERIODIC) {
+                if (iy == far)
+                    for (int i = 0; i < 9; ++i) f[i * pl + gc] = v[i];
+            } else if (iy == own) {
+                if (kind == BC_OUTFLOW)
+                    for (int i = 0; i < 9; ++i) f[i * pl + gc] = v[i];
+                else if (kind == BC_REFLECT)
+                    for (int i = 0; i < 9; ++i) f[i * pl + gc] = v[mirror_y(i)];
+                else
+                    for (int i = 0; i < 9; ++i) f[i * pl + gc] = G.feq[side][part][i];
+            }
+        }
+    }
+}
+
+// Status word bits (the same values as the LBM_FLAG_* of lbm.h).
+constexpr unsigned ST_NONPHYSICAL = 1u;  // rho <= 0 or a non-finite moment
+constexpr unsigned ST_TIMEOUT = 2u;      // a bounded device wait gave up
+constexpr unsigned ST_T_NONPOS = 4u;     // T <= 0 at some node (transient, allowed)
+
+// Health bits of one node's moments.
+template <typename S>
+__device__ __forceinline__ unsigned health(S rho, S ux, S uy, S T) {
+    if (!(rho > S(0)) || !isfinite(T) || !isfinite(ux + uy)) return ST_NONPHYSICAL;
+    return T > S(0) ? 0u : ST_T_NONPOS;
+}
+
+// OR the bits of all active lanes into the status word with one atomic per
+// warp, and only when some lane has a bit set.
+__device__ __forceinline__ void report(unsigned* status, unsigned bits) {
+    const unsigned m = __activemask();
+    const unsigned any = __reduce_or_sync(m, bits);
+    if (any && (threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicOr(status, any);
+}
+
+}  // namespace lbm

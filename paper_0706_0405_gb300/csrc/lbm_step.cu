@@ -1,0 +1,247 @@
+// lbm_step.cu -- the fused time step of the KT D2V9 finite-difference lattice
+// Boltzmann scheme with dissipation (Pan, Xu, Zhang & Jiang, IJMPC 2007,
+// Eq. SEC-VON-11): moments (Eqs. e4, e5, e7) -> equilibrium (Eqs. e16-e18)
+// -> beta-upwind first and central second differences (Eqs. SEC-VON-2a/2b)
+// -> BGK relaxation and forward-Euler update, one pass over the grid, with the
+// next level's ghost layer written by the edge nodes in the same pass.
+#include "lbm_launch.h"
+#include "lbm_ptx.cuh"
+
+namespace lbm {
+
+// One thread per node.  Each thread reads its node and the four star
+// neighbours of all nine populations (the neighbours come from L1/L2: the
+// same line serves the adjacent threads), computes the update in registers and
+// writes nine values.
+template <typename S, int TM>
+__global__ void __launch_bounds__(256) k_step_simple(const S* __restrict__ fin, S* __restrict__ fout,
+                                                     const Model<S> M, const Grid<S> G,
+                                                     long long level, unsigned* status) {
+    const int ix = blockIdx.x * blockDim.x + threadIdx.x;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix >= G.nx || iy >= G.ny) return;
+    const size_t pl = (size_t)G.plane;
+    const size_t c = cell(G, ix, iy);
+    S f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = __ldg(fin + i * pl + c);
+    S rho, ux, uy, T;
+    moments<S, TM>(f, M, rho, ux, uy, T);
+    report(status, health(rho, ux, uy, T));
+    S fe[9];
+    equilibrium(M, rho, ux, uy, T, fe);
+    S o[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const S* p = fin + i * pl + c;
+        o[i] = update(M, i, fe[i], f[i], __ldg(p + 1), __ldg(p - 1), __ldg(p + G.pitch),
+                      __ldg(p - G.pitch));
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fout[i * pl + c] = o[i];
+    if (ix == 0 || iy == 0 || ix == G.nx - 1 || iy == G.ny - 1)
+        write_ghosts(G, fout, ix, iy, o, level + 1);
+}
+
+// ------------------------------------------------------ FP32 ring kernel
+// Each CTA owns TX consecutive columns ("strip") and marches up a contiguous
+// run of rows of that strip (the runs of all CTAs tile the flattened
+// (strip, row) sequence evenly, so one wave of CTAs covers the grid with no
+// tail).  Rows of all nine planes, with 4 extra columns on each side, are
+// brought into a ring of R shared-memory slots by bulk asynchronous copies
+// (one per plane row) that complete on one mbarrier per slot; thread t keeps
+// the rows y-1, y, y+1 of its own column in registers and reads the x
+// neighbours of row y from the slot.  Every wait is bounded: on give-up the
+// CTA raises ST_TIMEOUT, drains its copies in flight (again bounded) and
+// returns.
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+template <int TX, int R, int TM>
+__global__ void __launch_bounds__(TX, 2)
+    k_step_ring(const float* __restrict__ fin, float* __restrict__ fout, const Model<float> M,
+                const Grid<float> G, long long level, unsigned* status, int rows_per_cta, int nstrips) {
+    constexpr int WPAD = TX + 8;  // floats per plane row in a slot: interior columns x0-4 .. x0+TX+3
+    extern __shared__ __align__(128) unsigned char smem[];
+    float* ring = reinterpret_cast<float*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(float) * R * 9 * WPAD);
+    __shared__ int abort_flag;
+
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int r = 0; r < R; ++r) mbar_init(&bar[r], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+
+    const size_t pl = (size_t)G.plane;
+    const long long total = (long long)nstrips * G.ny;
+    const long long w_begin = (long long)blockIdx.x * rows_per_cta;
+    const long long w_end = min(w_begin + (long long)rows_per_cta, total);
+    long long L = 0;  // row loads issued so far by this CTA (slot = L % R, parity = (L / R) & 1)
+
+    for (long long w = w_begin; w < w_end;) {
+        const int strip = (int)(w / G.ny);
+        const int y0 = (int)(w % G.ny);
+        const int n = (int)min((long long)(G.ny - y0), w_end - w);  // rows computed in this segment
+        const int x0 = strip * TX;
+        const int ix = x0 + tid;
+        const uint32_t bytes = (uint32_t)min(WPAD, G.pitch - x0) * (uint32_t)sizeof(float);
+        // load k (0 .. n+1) brings array row y0 + k, i.e. interior row y0 - 1 + k
+        auto issue = [&](int k) {
+            const long long q = L + k;
+            const int slot = (int)(q % R);
+            mbar_arrive_expect_tx(&bar[slot], 9u * bytes);
+            const float* src = fin + (size_t)(y0 + k) * G.pitch + x0;
+            float* dst = ring + (size_t)slot * 9 * WPAD;
+#pragma unroll
+            for (int i = 0; i < 9; ++i) bulk_g2s(dst + i * WPAD, src + i * pl, bytes, &bar[slot]);
+        };
+        auto slot_of = [&](int k) { return ring + (size_t)((L + k) % R) * 9 * WPAD; };
+        auto wait = [&](int k) -> bool {
+            const long long q = L + k;
+            return mbar_wait_bounded(&bar[q % R], (uint32_t)((q / R) & 1), kWaitLimit);
+        };
+        const int nload = n + 2;
+        int issued = min(R, nload);
+        __syncthreads();  // the previous segment is done with every slot
+        if (tid == 0)
+            for (int k = 0; k < issued; ++k) issue(k);
+
+        float S[9], C[9], N[9];
+        bool ok = wait(0);
+        if (ok) {
+            const float* sl = slot_of(0);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) S[i] = sl[i * WPAD + tid + 4];
+        }
+        ok = ok && wait(1);
+        if (ok) {
+            const float* sl = slot_of(1);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) C[i] = sl[i * WPAD + tid + 4];
+        }
+        if (!ok) abort_flag = 1;
+        int waited = ok ? 2 : 0;
+
+        for (int k = 1; k <= n; ++k) {
+            __syncthreads();  // slot of load k-1 is free; abort_flag is visible
+            if (abort_flag) {
+                // drain the copies this CTA still has in flight, then leave
+                for (int q = waited; q < issued; ++q) wait(q);
+                if (tid == 0) atomicOr(status, ST_TIMEOUT);
+                return;
+            }
+            if (tid == 0 && k - 1 + R < nload) {
+                issue(k - 1 + R);
+                ++issued;
+            } else if (k - 1 + R < nload) {
+                ++issued;
+            }
+            if (!wait(k + 1)) {
+                abort_flag = 1;
+                continue;
+            }
+            waited = k + 2;
+            const float* sc = slot_of(k);
+            const float* sn = slot_of(k + 1);
+            const int iy = y0 + k - 1;
+            if (ix < G.nx) {
+                float f[9], o[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) {
+                    N[i] = sn[i * WPAD + tid + 4];
+                    f[i] = C[i];
+                }
+                float rho, ux, uy, T;
+                moments<float, TM>(f, M, rho, ux, uy, T);
+                report(status, health(rho, ux, uy, T));
+                float fe[9];
+                equilibrium(M, rho, ux, uy, T, fe);
+#pragma unroll
+                for (int i = 0; i < 9; ++i)
+                    o[i] = update(M, i, fe[i], C[i], sc[i * WPAD + tid + 5], sc[i * WPAD + tid + 3],
+                                  N[i], S[i]);
+                const size_t c = cell(G, ix, iy);
+#pragma unroll
+                for (int i = 0; i < 9; ++i) fout[i * pl + c] = o[i];
+                if (ix == 0 || iy == 0 || ix == G.nx - 1 || iy == G.ny - 1)
+                    write_ghosts(G, fout, ix, iy, o, level + 1);
+            }
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                S[i] = C[i];
+                C[i] = N[i];
+            }
+        }
+        __syncthreads();
+        if (abort_flag) {
+            for (int q = waited; q < issued; ++q) wait(q);
+            if (tid == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
+        L += nload;
+        w += n;
+    }
+}
+
+template <int TX, int R>
+constexpr size_t ring_smem_bytes() {
+    return sizeof(float) * R * 9 * (TX + 8) + sizeof(uint64_t) * R;
+}
+
+template <int TX, int R, int TM>
+cudaError_t launch_ring(const float* fin, float* fout, const Model<float>& M, const Grid<float>& G,
+                        long long level, unsigned* status, int grid_hint, cudaStream_t st) {
+    constexpr size_t smem = ring_smem_bytes<TX, R>();
+    auto kern = k_step_ring<TX, R, TM>;
+    if (smem > 48 * 1024) {
+        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+    }
+    int grid = grid_hint;
+    if (grid <= 0) {
+        static int full_wave = 0;  // SMs x resident CTAs per SM, found once per instantiation
+        if (full_wave == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX, smem);
+            full_wave = sms * (per_sm > 0 ? per_sm : 1);
+        }
+        grid = full_wave;
+    }
+    const int nstrips = (G.nx + TX - 1) / TX;
+    const long long total = (long long)nstrips * G.ny;
+    const int rows_per_cta = (int)((total + grid - 1) / grid);
+    grid = (int)((total + rows_per_cta - 1) / rows_per_cta);
+    kern<<<grid, TX, smem, st>>>(fin, fout, M, G, level, status, rows_per_cta, nstrips);
+    return cudaGetLastError();
+}
+
+template <typename S, int TM>
+cudaError_t launch_step(const S* fin, S* fout, const Model<S>& M, const Grid<S>& G,
+                        long long level, unsigned* status, cudaStream_t st, const StepConfig& cfg) {
+    if constexpr (sizeof(S) == 4) {
+        if (cfg.variant == STEP_RING) {
+            if (cfg.tx == 128) return launch_ring<128, 4, TM>(fin, fout, M, G, level, status, cfg.grid, st);
+            if (cfg.ring == 6) return launch_ring<256, 6, TM>(fin, fout, M, G, level, status, cfg.grid, st);
+            return launch_ring<256, 4, TM>(fin, fout, M, G, level, status, cfg.grid, st);
+        }
+    }
+    dim3 block(64, 4);
+    dim3 grid((G.nx + block.x - 1) / block.x, (G.ny + block.y - 1) / block.y);
+    k_step_simple<S, TM><<<grid, block, 0, st>>>(fin, fout, M, G, level, status);
+    return cudaGetLastError();
+}
+
+#define LBM_STEP_INST(S, TM)                                                                     \
+    template cudaError_t launch_step<S, TM>(const S*, S*, const Model<S>&, const Grid<S>&,        \
+                                            long long, unsigned*, cudaStream_t, const StepConfig&);
+LBM_STEP_INST(double, T_PLAIN)
+LBM_STEP_INST(float, T_INT32)
+LBM_STEP_INST(float, T_INT64)
+LBM_STEP_INST(float, T_DF)
+#undef LBM_STEP_INST
+
+}  // namespace lbm

@@ -1,0 +1,335 @@
+"""ctypes binding of ``liblbm.so`` (C ABI in ``include/lbm.h``).
+
+The module-level functions carry the C names and only marshal arguments:
+pointers may be given as torch tensors, numpy arrays, integers or None.  All
+computation runs in the CUDA library; there is no CPU path.  If the library
+cannot be loaded, every call raises.
+
+``Lattice`` wraps one context for a problem description (the attributes of
+``workloads.Problem``) and converts results to numpy/torch.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+
+from . import build as _build
+
+LBM_OK, LBM_E_INVAL, LBM_E_NOMEM, LBM_E_CUDA, LBM_E_NONPHYSICAL, LBM_E_TIMEOUT, LBM_E_STATE = \
+    0, -1, -2, -3, -4, -5, -6
+STATUS_NAMES = {0: "LBM_OK", -1: "LBM_E_INVAL", -2: "LBM_E_NOMEM", -3: "LBM_E_CUDA",
+                -4: "LBM_E_NONPHYSICAL", -5: "LBM_E_TIMEOUT", -6: "LBM_E_STATE"}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_t64": 2, "fp32_tdf": 3}
+BC_KINDS = {"periodic": 0, "outflow": 1, "dirichlet": 2, "reflect": 3}
+
+# Exported symbols of include/lbm.h.
+EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init", "lbm_step", "lbm_moments",
+           "lbm_conservation", "lbm_sync", "lbm_get_f", "lbm_set_f", "lbm_step_count",
+           "lbm_checkpoint_bytes", "lbm_save", "lbm_load", "lbm_version", "lbm_health",
+           "lbm_set_launch", "lbm_get_launch", "lbm_autotune")
+LBM_FLAG_NONPHYSICAL, LBM_FLAG_TIMEOUT, LBM_FLAG_T_NONPOSITIVE = 1, 2, 4
+
+
+class LbmError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {message}")
+        self.status = status
+
+
+class lbm_bc(ctypes.Structure):
+    _fields_ = [("kind_lo", ctypes.c_int), ("kind_hi", ctypes.c_int),
+                ("split0", ctypes.c_double), ("split_speed", ctypes.c_double),
+                ("state_lo", ctypes.c_double * 4), ("state_hi", ctypes.c_double * 4)]
+
+
+class lbm_dvm(ctypes.Structure):
+    _fields_ = [("c1", ctypes.c_double), ("c2", ctypes.c_double), ("eta0", ctypes.c_double)]
+
+
+class lbm_dissipation(ctypes.Structure):
+    _fields_ = [("beta", ctypes.c_double), ("lambda_", ctypes.c_double * 9)]
+
+
+class lbm_launch(ctypes.Structure):
+    _fields_ = [("variant", ctypes.c_int), ("tx", ctypes.c_int), ("ring", ctypes.c_int),
+                ("grid", ctypes.c_int)]
+
+    def as_tuple(self):
+        return (self.variant, self.tx, self.ring, self.grid)
+
+
+_lib = None
+_VP = ctypes.c_void_p
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def load():
+    """Open liblbm.so (building it first if it is missing or stale)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build_library() if _build.stale() else _build.LIB
+    lib = ctypes.CDLL(path)
+    ctx = _VP
+    sig = {
+        "lbm_create": ([ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 +
+                       [ctypes.POINTER(lbm_dvm), ctypes.POINTER(lbm_dissipation),
+                        ctypes.POINTER(lbm_bc), ctypes.c_int, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+        "lbm_destroy": ([ctx], None),
+        "lbm_last_error": ([ctx], ctypes.c_char_p),
+        "lbm_init": ([ctx, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "lbm_step": ([ctx, ctypes.c_int], ctypes.c_int),
+        "lbm_moments": ([ctx, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "lbm_conservation": ([ctx, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "lbm_sync": ([ctx], ctypes.c_int),
+        "lbm_health": ([ctx, ctypes.POINTER(ctypes.c_uint)], ctypes.c_int),
+        "lbm_get_f": ([ctx, _VP], ctypes.c_int),
+        "lbm_set_f": ([ctx, _VP, ctypes.c_longlong], ctypes.c_int),
+        "lbm_step_count": ([ctx], ctypes.c_longlong),
+        "lbm_checkpoint_bytes": ([ctx], ctypes.c_size_t),
+        "lbm_save": ([ctx, _VP, ctypes.c_size_t], ctypes.c_int),
+        "lbm_load": ([ctx, _VP, ctypes.c_size_t], ctypes.c_int),
+        "lbm_version": ([], ctypes.c_char_p),
+        "lbm_set_launch": ([ctx, ctypes.POINTER(lbm_launch)], ctypes.c_int),
+        "lbm_get_launch": ([ctx, ctypes.POINTER(lbm_launch)], ctypes.c_int),
+        "lbm_autotune": ([ctx, ctypes.c_int, ctypes.POINTER(lbm_launch),
+                          ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+    }
+    for name, (args, res) in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = res
+    _lib = lib
+    return lib
+
+
+def _ptr(x):
+    """Address of a torch tensor / numpy array / int / None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_contiguous():
+            raise ValueError("tensors passed to liblbm must be contiguous")
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        if not x.flags.c_contiguous:
+            raise ValueError("arrays passed to liblbm must be C-contiguous")
+        return x.ctypes.data
+    raise TypeError(f"cannot pass {type(x).__name__} as a pointer")
+
+
+def _check(ctx, status):
+    if status != LBM_OK:
+        raise LbmError(status, load().lbm_last_error(ctx).decode())
+    return status
+
+
+# ------------------------------------------------------------- C-ABI calls
+
+def lbm_version() -> str:
+    return load().lbm_version().decode()
+
+
+def lbm_create(nx, ny, b, tau, dt, dx, dvm, diss, bc, prec, stream=None):
+    """Returns the context handle (int).  ``bc`` is a sequence of 4 lbm_bc."""
+    lib = load()
+    arr = (lbm_bc * 4)(*bc)
+    out = _VP()
+    st = lib.lbm_create(int(nx), int(ny), float(b), float(tau), float(dt), float(dx),
+                        ctypes.byref(dvm), ctypes.byref(diss), arr,
+                        PRECISIONS.get(prec, prec) if isinstance(prec, str) else int(prec),
+                        _ptr(stream), ctypes.byref(out))
+    _check(None, st)
+    return out.value
+
+
+def lbm_destroy(ctx) -> None:
+    load().lbm_destroy(ctx)
+
+
+def lbm_last_error(ctx=None) -> str:
+    return load().lbm_last_error(ctx).decode()
+
+
+def lbm_init(ctx, rho, ux, uy, T):
+    return _check(ctx, load().lbm_init(ctx, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(T)))
+
+
+def lbm_step(ctx, n):
+    return _check(ctx, load().lbm_step(ctx, int(n)))
+
+
+def lbm_moments(ctx, rho, ux, uy, T):
+    return _check(ctx, load().lbm_moments(ctx, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(T)))
+
+
+def lbm_conservation(ctx):
+    out = (ctypes.c_double * 4)()
+    _check(ctx, load().lbm_conservation(ctx, out))
+    return np.array(out[:])
+
+
+def lbm_sync(ctx):
+    return _check(ctx, load().lbm_sync(ctx))
+
+
+def lbm_health(ctx) -> int:
+    flags = ctypes.c_uint(0)
+    _check(ctx, load().lbm_health(ctx, ctypes.byref(flags)))
+    return int(flags.value)
+
+
+def lbm_get_f(ctx, dst):
+    return _check(ctx, load().lbm_get_f(ctx, _ptr(dst)))
+
+
+def lbm_set_f(ctx, src, step=0):
+    return _check(ctx, load().lbm_set_f(ctx, _ptr(src), int(step)))
+
+
+def lbm_step_count(ctx) -> int:
+    return int(load().lbm_step_count(ctx))
+
+
+def lbm_checkpoint_bytes(ctx) -> int:
+    return int(load().lbm_checkpoint_bytes(ctx))
+
+
+def lbm_save(ctx, buf, nbytes):
+    return _check(ctx, load().lbm_save(ctx, _ptr(buf), int(nbytes)))
+
+
+def lbm_load(ctx, buf, nbytes):
+    return _check(ctx, load().lbm_load(ctx, _ptr(buf), int(nbytes)))
+
+
+def lbm_set_launch(ctx, variant, tx=256, ring=4, grid=0):
+    return _check(ctx, load().lbm_set_launch(ctx, ctypes.byref(lbm_launch(variant, tx, ring, grid))))
+
+
+def lbm_get_launch(ctx):
+    out = lbm_launch()
+    _check(ctx, load().lbm_get_launch(ctx, ctypes.byref(out)))
+    return out.as_tuple()
+
+
+def lbm_autotune(ctx, steps=20):
+    """Returns (chosen (variant, tx, ring, grid), per-candidate ms per step)."""
+    best = lbm_launch()
+    ms = (ctypes.c_double * 8)()
+    n = ctypes.c_int(0)
+    _check(ctx, load().lbm_autotune(ctx, int(steps), ctypes.byref(best), ms, ctypes.byref(n)))
+    return best.as_tuple(), list(ms[: n.value])
+
+
+# ------------------------------------------------------------ convenience
+
+def make_bc(side) -> lbm_bc:
+    b = lbm_bc()
+    b.kind_lo = BC_KINDS[side.kind_lo]
+    b.kind_hi = BC_KINDS[side.kind_hi]
+    b.split0 = float(side.split0)
+    b.split_speed = float(side.split_speed)
+    for q in range(4):
+        b.state_lo[q] = float(side.state_lo[q])
+        b.state_hi[q] = float(side.state_hi[q])
+    return b
+
+
+class Lattice:
+    """One liblbm context for a problem (attributes of workloads.Problem).
+
+    ``stream`` defaults to torch's current CUDA stream.  Results come back as
+    torch CUDA tensors of the storage dtype (or numpy when asked)."""
+
+    def __init__(self, p, precision: str = "fp64", stream=None):
+        import torch
+        self.p = p
+        self.precision = precision
+        self.dtype = torch.float64 if precision == "fp64" else torch.float32
+        self.np_dtype = np.float64 if precision == "fp64" else np.float32
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.stream = stream
+        dvm = lbm_dvm(p.c1, p.c2, p.eta0)
+        diss = lbm_dissipation()
+        diss.beta = float(p.beta)
+        for i in range(9):
+            diss.lambda_[i] = float(p.lam[i])
+        self.ctx = lbm_create(p.nx, p.ny, p.b, p.tau, p.dt, p.dx, dvm, diss,
+                              [make_bc(s) for s in p.sides], precision, stream)
+
+    def close(self):
+        if self.ctx:
+            lbm_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def _dev(self, a):
+        import torch
+        if isinstance(a, torch.Tensor):
+            return a.to(device="cuda", dtype=self.dtype).contiguous()
+        return torch.as_tensor(np.ascontiguousarray(a, dtype=self.np_dtype), device="cuda")
+
+    def init(self, rho, ux, uy, T):
+        ts = [self._dev(a) for a in (rho, ux, uy, T)]
+        lbm_init(self.ctx, *ts)
+        self._keep = ts  # inputs live at least until the queued kernel ran
+        return self
+
+    def step(self, n: int):
+        lbm_step(self.ctx, n)
+        return self
+
+    def sync(self):
+        lbm_sync(self.ctx)
+
+    def health(self) -> int:
+        return lbm_health(self.ctx)
+
+    @property
+    def step_count(self) -> int:
+        return lbm_step_count(self.ctx)
+
+    def moments(self):
+        import torch
+        out = [torch.empty((self.p.ny, self.p.nx), dtype=self.dtype, device="cuda") for _ in range(4)]
+        lbm_moments(self.ctx, *out)
+        lbm_sync(self.ctx)
+        return out
+
+    def conservation(self):
+        return lbm_conservation(self.ctx)
+
+    def get_f(self):
+        import torch
+        out = torch.empty((9, self.p.ny, self.p.nx), dtype=self.dtype, device="cuda")
+        lbm_get_f(self.ctx, out)
+        torch.cuda.synchronize()
+        return out
+
+    def set_f(self, f, step: int = 0):
+        t = self._dev(f)
+        lbm_set_f(self.ctx, t, step)
+        self._keep = [t]
+        return self
+
+
+__all__ = ["LbmError", "Lattice", "EXPORTS", "PRECISIONS", "load", "library_path"] + list(EXPORTS)

@@ -1,0 +1,91 @@
+"""Host-side checks of the C ABI (no GPU compute): the library loads, exports
+every entry point include/lbm.h declares, and rejects invalid arguments with
+LBM_E_INVAL before touching the device."""
+import math
+import os
+import re
+import subprocess
+
+import pytest
+
+from paper_0706_0405_gb300 import lbm
+from paper_0706_0405_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    names = set()
+    for fn in os.listdir(os.path.join(ROOT, "include")):
+        if fn.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", fn)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names |= set(re.findall(r"\b(lbm_[a-z0-9_]+)\s*\(", src))
+    return names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = lbm.load()
+    declared = _declared()
+    assert declared, "no declarations found"
+    out = subprocess.run(["nm", "-D", "--defined-only", lbm.library_path()], capture_output=True,
+                         text=True).stdout
+    exported = set(re.findall(r" T (lbm_[a-z0-9_]+)$", out, flags=re.M))
+    assert declared <= exported, declared - exported
+    for name in declared:
+        assert hasattr(lib, name)
+    assert set(lbm.EXPORTS) <= declared
+
+
+def test_library_is_built_for_sm103a():
+    from paper_0706_0405_gb300 import build as B
+    assert "arch=compute_103a,code=sm_103a" in B.ARCH
+
+
+def _args(p, **over):
+    dvm = lbm.lbm_dvm(over.get("c1", p.c1), over.get("c2", p.c2), over.get("eta0", p.eta0))
+    diss = lbm.lbm_dissipation()
+    diss.beta = over.get("beta", p.beta)
+    lam = over.get("lam", p.lam)
+    for i in range(9):
+        diss.lambda_[i] = lam[i]
+    sides = over.get("sides", p.sides)
+    return (over.get("nx", p.nx), over.get("ny", p.ny), over.get("b", p.b), over.get("tau", p.tau),
+            over.get("dt", p.dt), over.get("dx", p.dx), dvm, diss, [lbm.make_bc(s) for s in sides],
+            over.get("prec", 0))
+
+
+@pytest.mark.parametrize("over,msg", [
+    ({"nx": 0}, "nx and ny"), ({"ny": -3}, "nx and ny"), ({"b": 0.0}, "b must"),
+    ({"tau": -1.0}, "tau"), ({"dt": math.nan}, "dt"), ({"dx": 0.0}, "dx"),
+    ({"c1": 9.0}, "singular"), ({"eta0": 0.0}, "eta0"), ({"beta": 0.6}, "beta"),
+    ({"beta": -0.1}, "beta"), ({"lam": (0.1,) * 8 + (-1.0,)}, "lambda[8]"), ({"prec": 7}, "precision"),
+    ({"sides": (W.Side("periodic"), W.Side("outflow"), W.Side("periodic"), W.Side("periodic"))},
+     "periodic"),
+    ({"sides": (W.Side("outflow"),) * 3 + (W.Side("dirichlet", state_lo=(-1.0, 0, 0, 1.0)),)},
+     "Dirichlet"),
+])
+def test_create_rejects_invalid_arguments(over, msg):
+    p = W.sod_400x4()
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create(*_args(p, **over))
+    assert ei.value.status == lbm.LBM_E_INVAL
+    assert msg in str(ei.value)
+
+
+def test_calls_on_null_context_fail_cleanly():
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_step(None, 1)
+    assert ei.value.status == lbm.LBM_E_INVAL
+    assert lbm.lbm_step_count(None) == -1
+    assert lbm.lbm_checkpoint_bytes(None) == 0
+    lbm.lbm_destroy(None)
+
+
+def test_create_without_gpu_reports_cuda_error():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create(*_args(W.sod_400x4()))
+    assert ei.value.status in (lbm.LBM_E_CUDA, lbm.LBM_E_NOMEM)
