@@ -218,6 +218,34 @@ lbm_status lbm_get_launch(const lbm_ctx* ctx, lbm_launch* launch);
  * at most 8, stored in *n_candidates if not NULL). */
 lbm_status lbm_autotune(lbm_ctx* ctx, int steps, lbm_launch* best, double* ms, int* n_candidates);
 
+/* FP64 conservation totals (out[0..3] = sum rho, sum rho ux, sum rho uy,
+ * sum rho (b T + u^2), as lbm_conservation) of a dense 9 x ny x nx
+ * distribution f in device memory (the layout lbm_get_f writes; element type
+ * double for LBM_FP64, float for the FP32 modes), for callers that cannot
+ * allocate device memory: a process whose device memory is committed to a
+ * fixed pool or a framework's caching allocator, a latency-critical loop in
+ * which an allocation could synchronise and stall the device, a host with a
+ * fixed device-memory budget.  No context is needed and nothing is
+ * allocated.  The paper has no counterpart; this is a service of the library.
+ *  - Scratch: a fixed device array inside the library (64 KiB + 32 B), held on
+ *    every GPU that loads the library until the process exits.  It bounds
+ *    nx * ny to 8 388 608 nodes (2048 tiles of 4096); larger grids get
+ *    LBM_E_INVAL.
+ *  - The first call on each device looks up that array's device address (a
+ *    one-time set-up, with the device current); make that first call before
+ *    any stream capture.
+ *  - All calls share the array; calls that overlap on the GPU race and may
+ *    return wrong totals.  Each call writes every value it reads, so a call
+ *    never depends on an earlier call's contents.
+ *  - Work runs on `stream` (a cudaStream_t, NULL = legacy default stream),
+ *    after whatever the caller queued there; the call synchronises that
+ *    stream and writes out (host or device memory) before returning.
+ *  - Errors: LBM_E_INVAL (NULL pointer, nx or ny < 1, too many nodes, unknown
+ *    precision), LBM_E_CUDA (launch or copy failed).  lbm_last_error does not
+ *    describe errors of this call. */
+lbm_status lbm_conservation_noalloc(const void* f, int nx, int ny, lbm_precision prec,
+                                    const lbm_dvm* dvm, double out[4], void* stream);
+
 /* Version string of the library. */
 const char* lbm_version(void);
 

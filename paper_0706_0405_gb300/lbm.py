@@ -27,7 +27,7 @@ BC_KINDS = {"periodic": 0, "outflow": 1, "dirichlet": 2, "reflect": 3}
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init", "lbm_step", "lbm_moments",
            "lbm_conservation", "lbm_sync", "lbm_get_f", "lbm_set_f", "lbm_step_count",
            "lbm_checkpoint_bytes", "lbm_save", "lbm_load", "lbm_version", "lbm_health",
-           "lbm_set_launch", "lbm_get_launch", "lbm_autotune")
+           "lbm_set_launch", "lbm_get_launch", "lbm_autotune", "lbm_conservation_noalloc")
 LBM_FLAG_NONPHYSICAL, LBM_FLAG_TIMEOUT, LBM_FLAG_T_NONPOSITIVE = 1, 2, 4
 
 
@@ -95,6 +95,9 @@ def load():
         "lbm_load": ([ctx, _VP, ctypes.c_size_t], ctypes.c_int),
         "lbm_version": ([], ctypes.c_char_p),
         "lbm_set_launch": ([ctx, ctypes.POINTER(lbm_launch)], ctypes.c_int),
+        "lbm_conservation_noalloc": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.POINTER(lbm_dvm), ctypes.POINTER(ctypes.c_double), _VP],
+                                     ctypes.c_int),
         "lbm_get_launch": ([ctx, ctypes.POINTER(lbm_launch)], ctypes.c_int),
         "lbm_autotune": ([ctx, ctypes.c_int, ctypes.POINTER(lbm_launch),
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
@@ -207,6 +210,18 @@ def lbm_save(ctx, buf, nbytes):
 
 def lbm_load(ctx, buf, nbytes):
     return _check(ctx, load().lbm_load(ctx, _ptr(buf), int(nbytes)))
+
+
+def lbm_conservation_noalloc(f, nx, ny, prec, dvm, stream=None):
+    """Totals of a dense 9 x ny x nx device distribution without allocating
+    (see include/lbm.h); returns a numpy array of 4 doubles."""
+    out = (ctypes.c_double * 4)()
+    st = load().lbm_conservation_noalloc(
+        _ptr(f), int(nx), int(ny), PRECISIONS.get(prec, prec) if isinstance(prec, str) else int(prec),
+        ctypes.byref(dvm), out, _ptr(stream))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_conservation_noalloc failed")
+    return np.array(out[:])
 
 
 def lbm_set_launch(ctx, variant, tx=256, ring=4, grid=0):
