@@ -194,15 +194,56 @@ size_t lbm_checkpoint_bytes(const lbm_ctx* ctx);
 lbm_status lbm_save(lbm_ctx* ctx, void* buf, size_t bytes);
 lbm_status lbm_load(lbm_ctx* ctx, const void* buf, size_t bytes);
 
+/* ------------------------------------------------------------- adjoint
+ * The adjoint of lbm_step is the transpose of the linearised update of
+ * Eq. (SEC-VON-11): the transposed five-point star, the ghost links routed
+ * back through the boundary rule (outflow and reflect feed the edge node,
+ * periodic wraps, Dirichlet feeds nothing) and the transposed Jacobian of
+ * f -> f^eq(moments(f)) (Eqs. e4, e5, e7, e16-e18).  Adjoint arrays are
+ * dense 9 x ny x nx of the storage type (FP32 contexts use an FP32 adjoint).
+ *
+ * lbm_record(ctx, K): keep a copy of the current level now and of every K-th
+ * level lbm_step produces from here (K = 0 stops recording); memory grows by
+ * one level per K steps.  lbm_init / lbm_set_f / lbm_load stop recording. */
+lbm_status lbm_record(lbm_ctx* ctx, int every);
+
+/* Seed the adjoint of the current level from adjoints of its moments:
+ * abar_j = sum_m qbar_m d q_m / d f_j with q = (rho, ux, uy, T); any qbar may
+ * be NULL (zero).  qbar are ny x nx fields, abar a 9 x ny x nx output. */
+lbm_status lbm_adjoint_seed(lbm_ctx* ctx, const void* qbar_rho, const void* qbar_ux,
+                            const void* qbar_uy, const void* qbar_T, void* abar);
+
+/* Apply n adjoint steps: abar (in: adjoint of the current level k; out:
+ * adjoint of level k - n).  Levels are recomputed from the checkpoint that
+ * starts each segment of K steps (memory K + 2 levels besides the
+ * checkpoints).  *dL_dtau (host, may be NULL) is incremented by the tau
+ * derivative of these n steps, d out_i / d tau = -(dt / tau^2) (f^eq_i - f_i).
+ * Afterwards the context's current level is k - n.  LBM_E_STATE without a
+ * recording, LBM_E_INVAL if fewer than n steps are recorded. */
+lbm_status lbm_adjoint_step(lbm_ctx* ctx, int n, void* abar, double* dL_dtau);
+
+/* Gradient with respect to the fields of an initial condition f = f^eq(q):
+ * g_m = sum_i abar_i d f^eq_i / d q_m at the fields q = (rho, ux, uy, T);
+ * any output may be NULL. */
+lbm_status lbm_feq_vjp(lbm_ctx* ctx, const void* rho, const void* ux, const void* uy, const void* T,
+                       const void* abar, void* g_rho, void* g_ux, void* g_uy, void* g_T);
+
 /* Launch shape of the step kernel. */
 typedef struct lbm_launch {
     int variant; /* 0: one thread per node, neighbours read through L1/L2;
                     1: FP32 modes only: CTAs own column strips and march up a
                     balanced run of rows, rows of all nine planes staged in a
-                    shared-memory ring by bulk asynchronous copies */
-    int tx;      /* variant 1: columns per CTA, 128 or 256 */
+                    shared-memory ring by bulk asynchronous copies;
+                    2: FP32 modes only: each thread updates tx x-adjacent
+                    nodes with vector loads and stores;
+                    3: FP32 modes only (default): persistent CTAs of 64 x 8
+                    threads; each 64 x 8 tile plus its halo (72 x 10 x 9
+                    planes) arrives in shared memory by one tiled tensor copy
+                    (TMA), double-buffered, and the stencil reads shared
+                    memory */
+    int tx;      /* variant 1: columns per CTA, 128 or 256; variant 2: 2 or 4 */
     int ring;    /* variant 1: ring slots, 4 or 6 (4 when tx = 128) */
-    int grid;    /* variant 1: CTAs; 0 = one full wave (SMs x resident CTAs) */
+    int grid;    /* variants 1, 3: CTAs; 0 = one full wave (SMs x resident CTAs) */
 } lbm_launch;
 
 /* Set / read the launch shape used by lbm_step (LBM_E_INVAL for shapes the
@@ -215,7 +256,9 @@ lbm_status lbm_get_launch(const lbm_ctx* ctx, lbm_launch* launch);
  * restore the state and step counter the context had before.  Writes the
  * chosen shape to *best (may be NULL) and the per-step milliseconds of each
  * candidate to ms[0..n) if ms is not NULL (n = the number of candidates,
- * at most 8, stored in *n_candidates if not NULL). */
+ * at most 8, stored in *n_candidates if not NULL).  Candidates, in order:
+ * variant 0; for FP32 also (3), (2, 4), (2, 2), (1, 256, 4), (1, 256, 6),
+ * (1, 128, 4). */
 lbm_status lbm_autotune(lbm_ctx* ctx, int steps, lbm_launch* best, double* ms, int* n_candidates);
 
 /* FP64 conservation totals (out[0..3] = sum rho, sum rho ux, sum rho uy,
@@ -245,6 +288,58 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps, lbm_launch* best, double* ms, i
  *    describe errors of this call. */
 lbm_status lbm_conservation_noalloc(const void* f, int nx, int ny, lbm_precision prec,
                                     const lbm_dvm* dvm, double out[4], void* stream);
+
+/* --------------------------------------------------------------- batch
+ * Many independent problems (each with its own grid, constants and boundary
+ * kinds) advanced together by one persistent cooperative kernel launch per
+ * lbm_batch_step call: every CTA walks a static share of the list of
+ * (problem, 256 x 4 node tile) pairs each step and a bounded grid barrier
+ * separates the steps (LBM_E_TIMEOUT if it gives up).  The launch is captured
+ * once per step count into a CUDA graph on a stream private to the batch and
+ * replayed there, ordered after the batch's stream by events (so the legacy
+ * default stream works too); if capture fails the launch runs directly.  The per-node
+ * arithmetic is that of lbm_step, so every problem's levels equal those of
+ * stepping it alone.  FP32 modes only. */
+typedef struct lbm_problem {
+    int nx, ny;
+    double b, tau, dt, dx;
+    lbm_dvm dvm;
+    lbm_dissipation diss;
+    lbm_bc bc[4];
+} lbm_problem;
+
+typedef struct lbm_batch lbm_batch;
+
+lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision prec, void* stream,
+                            lbm_batch** out);
+void lbm_batch_destroy(lbm_batch* batch);
+const char* lbm_batch_last_error(const lbm_batch* batch);
+
+/* rho[p], ux[p], uy[p], T[p]: problem p's ny x nx fields (float); every
+ * problem is initialised and the batch's step counter reset to 0. */
+lbm_status lbm_batch_init(lbm_batch* batch, const void* const* rho, const void* const* ux,
+                          const void* const* uy, const void* const* T);
+
+/* Advance every problem n steps (asynchronous). */
+lbm_status lbm_batch_step(lbm_batch* batch, int n);
+
+/* Wait; LBM_E_NONPHYSICAL / LBM_E_TIMEOUT as for lbm_sync. */
+lbm_status lbm_batch_sync(lbm_batch* batch);
+
+/* The context of problem p (owned by the batch; use it for lbm_moments,
+ * lbm_get_f, lbm_conservation ... after lbm_batch_sync; do not destroy it). */
+lbm_ctx* lbm_batch_problem(lbm_batch* batch, int p);
+
+/* Launch facts: CTAs of the persistent launch, tiles per step, and 1 if the
+ * last lbm_batch_step ran from a CUDA graph (0 before any step, -1 if graph
+ * capture failed and the launch runs directly). */
+lbm_status lbm_batch_info(const lbm_batch* batch, int* grid, int* ntiles, int* graph);
+
+/* FP64 and FP32 FMA throughput (TFLOP/s, 2 flops per FMA) of the current
+ * device, from chains of dependent FMAs on every SM (~0.1 s).  Not from the
+ * paper: the benchmark's ceiling for the FP64 step, which is bounded by the
+ * FP64 pipe rather than by HBM on this part. */
+lbm_status lbm_probe_rates(double* fp64_tflops, double* fp32_tflops);
 
 /* Version string of the library. */
 const char* lbm_version(void);

@@ -87,6 +87,10 @@ def _load():
         lib.kt_step_nodes.argtypes = [cfgp, _D, ctypes.c_long, _L, ctypes.c_long, _D]
         lib.kt_fields.argtypes = [cfgp, _D, _D, _D, _D, _D]
         lib.kt_sums.argtypes = [cfgp, _D, _D]
+        lib.kt_feq_jacobian.argtypes = [cfgp, _D, _D]
+        lib.kt_feq_vjp.argtypes = [cfgp, _D, _D, _D]
+        lib.kt_moments_vjp.argtypes = [cfgp, _D, _D, _D]
+        lib.kt_adjoint_step.argtypes = [cfgp, _D, ctypes.c_long, _D, _D, _D]
         lib.kt_set_threads.argtypes = [ctypes.c_int]
         lib.kt_max_threads.restype = ctypes.c_int
         _lib = lib
@@ -206,6 +210,77 @@ def sums(p, f: np.ndarray) -> np.ndarray:
     return out
 
 
+def feq_jacobian(p, f9) -> np.ndarray:
+    """J[i, j] = d f^eq_i / d f_j at the nine populations f9 (chain rule
+    through the moments)."""
+    f9 = np.ascontiguousarray(f9, dtype=np.float64)
+    J = np.zeros(81)
+    c = config(p)
+    _load().kt_feq_jacobian(ctypes.byref(c), _ptr(f9), _ptr(J))
+    return J.reshape(9, 9)
+
+
+def feq_vjp(p, q, abar9) -> np.ndarray:
+    """sum_i abar_i d f^eq_i / d q for q = (rho, ux, uy, T)."""
+    q = np.ascontiguousarray(q, dtype=np.float64)
+    abar9 = np.ascontiguousarray(abar9, dtype=np.float64)
+    out = np.zeros(4)
+    c = config(p)
+    _load().kt_feq_vjp(ctypes.byref(c), _ptr(q), _ptr(abar9), _ptr(out))
+    return out
+
+
+def moments_vjp(p, f9, qbar) -> np.ndarray:
+    """sum_m qbar_m d q_m / d f at the populations f9."""
+    f9 = np.ascontiguousarray(f9, dtype=np.float64)
+    qbar = np.ascontiguousarray(qbar, dtype=np.float64)
+    out = np.zeros(9)
+    c = config(p)
+    _load().kt_moments_vjp(ctypes.byref(c), _ptr(f9), _ptr(qbar), _ptr(out))
+    return out
+
+
+def adjoint_step(p, f: np.ndarray, n: int, abar_next: np.ndarray):
+    """Adjoint of the step from level n (state f) to level n + 1: returns
+    (abar_n, dL/dtau contribution).  f's ghost layer is refilled."""
+    c = config(p)
+    abar = np.zeros_like(f)
+    an = np.ascontiguousarray(abar_next, dtype=np.float64)
+    dtau = np.zeros(1)
+    _load().kt_adjoint_step(ctypes.byref(c), _ptr(f), int(n), _ptr(an), _ptr(abar), _ptr(dtau))
+    return abar, float(dtau[0])
+
+
+def adjoint_run(p, initial, steps: int, qbar_final):
+    """Gradient of L through `steps` steps from f^0 = f^eq(initial), given
+    qbar_final = dL/d(rho, ux, uy, T) of the final level ((4, ny, nx)).
+    Stores every level (small problems only).  Returns
+    (dL/d fields (4, ny, nx), dL/d tau, final fields)."""
+    f = init(p, *initial)
+    levels = [f.copy()]
+    for n in range(steps):
+        g = levels[-1].copy()
+        run(p, g, 1, n)
+        levels.append(g)
+    fin = levels[-1]
+    abar = empty_state(p) * 0.0
+    qb = np.asarray(qbar_final, dtype=np.float64)
+    for k in range(p.ny):
+        for j in range(p.nx):
+            abar[:, k + 1, j + 1] = moments_vjp(p, fin[:, k + 1, j + 1], qb[:, k, j])
+    dtau = 0.0
+    for n in range(steps - 1, -1, -1):
+        abar, dt_n = adjoint_step(p, levels[n].copy(), n, abar)
+        dtau += dt_n
+    grads = np.zeros((4, p.ny, p.nx))
+    flds = [np.asarray(a, dtype=np.float64).reshape(p.ny, p.nx) for a in initial]
+    for k in range(p.ny):
+        for j in range(p.nx):
+            q = [flds[m][k, j] for m in range(4)]
+            grads[:, k, j] = feq_vjp(p, q, abar[:, k + 1, j + 1])
+    return grads, dtau, fields(p, fin)
+
+
 def interior(f: np.ndarray) -> np.ndarray:
     """The (9, ny, nx) interior of a state with ghost layer."""
     return f[:, 1:-1, 1:-1]
@@ -223,4 +298,5 @@ def default_lambda(c1: float, dx: float, scale: float = 1.0) -> np.ndarray:
 __all__ = [
     "config", "set_threads", "max_threads", "velocities", "feq", "moments", "empty_state",
     "init", "fill_ghosts", "run", "step_nodes", "fields", "sums", "interior", "default_lambda",
+    "feq_jacobian", "feq_vjp", "moments_vjp", "adjoint_step", "adjoint_run",
 ]

@@ -362,3 +362,210 @@ void kt_sums(const kt_config* c, const double* f, double out[4]) {
             }
     for (int q = 0; q < 4; ++q) out[q] = s[q];
 }
+
+/* ------------------------------------------------------------------------
+ * Adjoint (transpose of the linearised step).  Written from the same
+ * equations: the step is out_i(x) = sum over the star of coefficients times
+ * f_i(x + s), plus (dt / tau) f^eq_i(moments f(x)); its transpose scatters
+ * each coefficient times the adjoint of out_i(x) back to f_i(x + s) (through
+ * the ghost rule when x + s is a ghost cell) and adds
+ * (dt / tau) sum_i abar_i J_ij with J = d f^eq / d f at f(x).
+ * ---------------------------------------------------------------------- */
+
+/* d out_i(x) / d f_i(x + s) of Eqs. (SEC-VON-2a/2b, SEC-VON-11) for the star
+ * s = centre, +x, -x, +y, -y, without the f^eq term. */
+static void star_coeffs(const kt_config* c, int i, double coef[5]) {
+    double vx[9], vy[9];
+    kt_velocities(c->c1, c->c2, vx, vy);
+    double beta = c->beta, dt = c->dt, dx = c->dx, lam = c->lambda[i] * dt / (dx * dx);
+    double ax = vx[i] * dt / dx, ay = vy[i] * dt / dx;
+    double cE, cC, cW, cN, cS;
+    if (SX[i] >= 0) { /* -ax (beta fE + (1 - 2 beta) f0 - (1 - beta) fW) */
+        cE = -ax * beta;
+        cC = -ax * (1.0 - 2.0 * beta);
+        cW = ax * (1.0 - beta);
+    } else { /* -ax ((1 - beta) fE - (1 - 2 beta) f0 - beta fW) */
+        cE = -ax * (1.0 - beta);
+        cC = ax * (1.0 - 2.0 * beta);
+        cW = ax * beta;
+    }
+    if (SY[i] >= 0) {
+        cN = -ay * beta;
+        cC += -ay * (1.0 - 2.0 * beta);
+        cS = ay * (1.0 - beta);
+    } else {
+        cN = -ay * (1.0 - beta);
+        cC += ay * (1.0 - 2.0 * beta);
+        cS = ay * beta;
+    }
+    coef[0] = 1.0 + cC - 4.0 * lam - dt / c->tau;
+    coef[1] = cE + lam;
+    coef[2] = cW + lam;
+    coef[3] = cN + lam;
+    coef[4] = cS + lam;
+}
+
+/* Derivatives of f^eq_i (Eqs. e16-e18) with respect to q = (rho, ux, uy, T):
+ * dF[i][m]. */
+static void feq_dq(const kt_config* c, double rho, double ux, double uy, double T, double dF[9][4]) {
+    double b = c->b, c1s = c->c1 * c->c1, c2s = c->c2 * c->c2, e0s = c->eta0 * c->eta0;
+    double u2 = ux * ux + uy * uy;
+    double vx[9], vy[9];
+    kt_velocities(c->c1, c->c2, vx, vy);
+    /* A, B as written in Eqs. (e17), (e18) and their partial derivatives in T
+     * and in u^2. */
+    double q1 = 4.0 * (c1s - c2s), q5 = 4.0 * (c2s - c1s);
+    double A1 = (-c2s + ((b - 2.0) * c2s / e0s + 2.0) * T + c2s / c1s * u2) / q1;
+    double A5 = (-c1s + ((b - 2.0) * c1s / e0s + 2.0) * T + c1s / c2s * u2) / q5;
+    double A1T = ((b - 2.0) * c2s / e0s + 2.0) / q1, A1u = (c2s / c1s) / q1;
+    double A5T = ((b - 2.0) * c1s / e0s + 2.0) / q5, A5u = (c1s / c2s) / q5;
+    double d1 = 2.0 * c1s * (c1s - c2s), d5 = 2.0 * c2s * (c2s - c1s);
+    double B1 = (-c2s + (b + 2.0) * T + u2) / d1, B5 = (-c1s + (b + 2.0) * T + u2) / d5;
+    double B1T = (b + 2.0) / d1, B1u = 1.0 / d1, B5T = (b + 2.0) / d5, B5u = 1.0 / d5;
+    double D1 = 1.0 / (2.0 * c1s * c1s), D5 = 1.0 / (2.0 * c2s * c2s);
+    /* i = 0: F = rho (b - 2) T / eta0^2 */
+    dF[0][0] = (b - 2.0) * T / e0s;
+    dF[0][1] = 0.0;
+    dF[0][2] = 0.0;
+    dF[0][3] = rho * (b - 2.0) / e0s;
+    for (int i = 1; i < 9; ++i) {
+        double A = i <= 4 ? A1 : A5, AT = i <= 4 ? A1T : A5T, Au = i <= 4 ? A1u : A5u;
+        double B = i <= 4 ? B1 : B5, BT = i <= 4 ? B1T : B5T, Bu = i <= 4 ? B1u : B5u;
+        double D = i <= 4 ? D1 : D5;
+        double vu = vx[i] * ux + vy[i] * uy;
+        dF[i][0] = A + B * vu + D * vu * vu;
+        /* d/dux: A and B through u^2 (d u^2 / d ux = 2 ux), and v.u */
+        dF[i][1] = rho * (Au * 2.0 * ux + Bu * 2.0 * ux * vu + B * vx[i] + 2.0 * D * vu * vx[i]);
+        dF[i][2] = rho * (Au * 2.0 * uy + Bu * 2.0 * uy * vu + B * vy[i] + 2.0 * D * vu * vy[i]);
+        dF[i][3] = rho * (AT + BT * vu);
+    }
+}
+
+/* Derivatives of q = (rho, ux, uy, T) (Eqs. e4, e5, e7) with respect to f_j
+ * at the populations f: dq[m][j]. */
+static void moments_df(const kt_config* c, const double f[9], double dq[4][9]) {
+    double m[4], vx[9], vy[9];
+    kt_moments(c, f, m);
+    kt_velocities(c->c1, c->c2, vx, vy);
+    double rho = m[0], ux = m[1], uy = m[2], T = m[3];
+    for (int j = 0; j < 9; ++j) {
+        double eta = eta_of(c, j);
+        double dx = vx[j] - ux, dy = vy[j] - uy;
+        dq[0][j] = 1.0;
+        dq[1][j] = dx / rho;
+        dq[2][j] = dy / rho;
+        /* T = (E / rho - u.u) / b, E = sum f (v^2 + eta^2) */
+        dq[3][j] = (dx * dx + dy * dy + eta * eta - c->b * T) / (c->b * rho);
+    }
+}
+
+/* Jacobian J[i][j] = d f^eq_i / d f_j at the populations f. */
+void kt_feq_jacobian(const kt_config* c, const double f[9], double J[81]) {
+    double m[4], dF[9][4], dq[4][9];
+    kt_moments(c, f, m);
+    feq_dq(c, m[0], m[1], m[2], m[3], dF);
+    moments_df(c, f, dq);
+    for (int i = 0; i < 9; ++i)
+        for (int j = 0; j < 9; ++j) {
+            double s = 0.0;
+            for (int q = 0; q < 4; ++q) s += dF[i][q] * dq[q][j];
+            J[i * 9 + j] = s;
+        }
+}
+
+/* Vector-Jacobian products: qbar_m = sum_i abar_i dF_i/dq_m at the state q,
+ * and abar_j = sum_m qbar_m dq_m/df_j at the populations f. */
+void kt_feq_vjp(const kt_config* c, const double q[4], const double abar[9], double qbar[4]) {
+    double dF[9][4];
+    feq_dq(c, q[0], q[1], q[2], q[3], dF);
+    for (int m = 0; m < 4; ++m) {
+        double s = 0.0;
+        for (int i = 0; i < 9; ++i) s += abar[i] * dF[i][m];
+        qbar[m] = s;
+    }
+}
+
+void kt_moments_vjp(const kt_config* c, const double f[9], const double qbar[4], double abar[9]) {
+    double dq[4][9];
+    moments_df(c, f, dq);
+    for (int j = 0; j < 9; ++j) {
+        double s = 0.0;
+        for (int m = 0; m < 4; ++m) s += qbar[m] * dq[m][j];
+        abar[j] = s;
+    }
+}
+
+/* Route an adjoint contribution `val` aimed at population i of the ghost cell
+ * of `side` next to interior cell (k, j) (storage indices) to the interior
+ * cell(s) that ghost value was made from at time t. */
+static void ghost_adjoint(const kt_config* c, double* abar, int side, int i, int k, int j,
+                          double along, double t, double val) {
+    const kt_side* s = &c->side[side];
+    int lo = along < s->split0 + s->split_speed * t;
+    int kind = lo ? s->kind_lo : s->kind_hi;
+    switch (kind) {
+    case KT_PERIODIC:
+        if (side == KT_LEFT) abar[at(c, i, k, c->nx)] += val;
+        else if (side == KT_RIGHT) abar[at(c, i, k, 1)] += val;
+        else if (side == KT_BOTTOM) abar[at(c, i, c->ny, j)] += val;
+        else abar[at(c, i, 1, j)] += val;
+        break;
+    case KT_OUTFLOW:
+        abar[at(c, i, k, j)] += val;
+        break;
+    case KT_REFLECT:
+        abar[at(c, mirror(i, side == KT_LEFT || side == KT_RIGHT), k, j)] += val;
+        break;
+    default: /* Dirichlet: the ghost value does not depend on f */
+        break;
+    }
+}
+
+/* One adjoint step.  f: level-n state (its ghost layer is refilled for time
+ * n dt); abar_next: adjoint of level n + 1 (interior of the ghost-layer
+ * layout); abar: receives the adjoint of level n (same layout, ghosts zero).
+ * *dtau accumulates sum_x sum_i abar_next_i(x) d out_i(x) / d tau with
+ * d out_i / d tau = -(dt / tau^2) (f^eq_i - f_i). */
+void kt_adjoint_step(const kt_config* c, double* f, long n, const double* abar_next,
+                     double* abar, double* dtau) {
+    double t = (double)n * c->dt;
+    kt_fill_ghosts(c, f, t);
+    size_t len = kt_field_len(c);
+    for (size_t q = 0; q < len; ++q) abar[q] = 0.0;
+    double coef[9][5];
+    for (int i = 0; i < 9; ++i) star_coeffs(c, i, coef[i]);
+    double w = c->dt / c->tau, acc_tau = 0.0;
+    for (int k = 1; k <= c->ny; ++k)
+        for (int j = 1; j <= c->nx; ++j) {
+            double a[9], fc[9], J[81], m[4], feq[9];
+            for (int i = 0; i < 9; ++i) {
+                a[i] = abar_next[at(c, i, k, j)];
+                fc[i] = f[at(c, i, k, j)];
+            }
+            /* collision: (dt / tau) J^T a */
+            kt_feq_jacobian(c, fc, J);
+            for (int jj = 0; jj < 9; ++jj) {
+                double s = 0.0;
+                for (int i = 0; i < 9; ++i) s += a[i] * J[i * 9 + jj];
+                abar[at(c, jj, k, j)] += w * s;
+            }
+            /* tau */
+            kt_moments(c, fc, m);
+            kt_feq(c, m[0], m[1], m[2], m[3], feq);
+            for (int i = 0; i < 9; ++i) acc_tau += a[i] * (-(c->dt / (c->tau * c->tau)) * (feq[i] - fc[i]));
+            /* stencil links */
+            double x = ((double)(j - 1) + 0.5) * c->dx, y = ((double)(k - 1) + 0.5) * c->dx;
+            for (int i = 0; i < 9; ++i) {
+                abar[at(c, i, k, j)] += coef[i][0] * a[i];
+                if (j < c->nx) abar[at(c, i, k, j + 1)] += coef[i][1] * a[i];
+                else ghost_adjoint(c, abar, KT_RIGHT, i, k, j, y, t, coef[i][1] * a[i]);
+                if (j > 1) abar[at(c, i, k, j - 1)] += coef[i][2] * a[i];
+                else ghost_adjoint(c, abar, KT_LEFT, i, k, j, y, t, coef[i][2] * a[i]);
+                if (k < c->ny) abar[at(c, i, k + 1, j)] += coef[i][3] * a[i];
+                else ghost_adjoint(c, abar, KT_TOP, i, k, j, x, t, coef[i][3] * a[i]);
+                if (k > 1) abar[at(c, i, k - 1, j)] += coef[i][4] * a[i];
+                else ghost_adjoint(c, abar, KT_BOTTOM, i, k, j, x, t, coef[i][4] * a[i]);
+            }
+        }
+    *dtau += acc_tau;
+}

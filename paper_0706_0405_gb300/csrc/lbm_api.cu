@@ -7,6 +7,8 @@
 #include <cstring>
 #include <string>
 #include <type_traits>
+#include <vector>
+#include <string>
 
 #include "../../include/lbm.h"
 #include "lbm_launch.h"
@@ -40,6 +42,19 @@ struct lbm_ctx {
     Grid<double> gd{};
     Grid<float> gf{};
     StepConfig cfg{};
+    CUtensorMap tmap[2];  // FP32: tensor maps of the two level buffers (tile kernel)
+    bool tmap_ok = false;
+    // adjoint: checkpoints every ck_every steps from level ck_base
+    int ck_every = 0;
+    long long ck_base = -1;
+    std::vector<void*> ck;       // ck[k] holds level ck_base + k * ck_every (padded, with ghosts)
+    std::vector<void*> seg;      // recomputed levels of one segment
+    void* adj[2] = {nullptr, nullptr};
+    double* d_taup = nullptr;
+    double* h_taup = nullptr;
+    int ntaup = 0;
+    void* d_astage = nullptr;    // staging of the adjoint calls' host arguments
+    size_t astage_bytes = 0;
     std::string err;
 };
 
@@ -310,6 +325,67 @@ lbm_status device_view(lbm_ctx* c, const void* p, size_t bytes, size_t offset, c
     return LBM_OK;
 }
 
+size_t level_bytes(const lbm_ctx* c) { return (size_t)9 * (size_t)c->plane * c->esize; }
+
+// Keep a copy of the current level (padded, ghosts included) as checkpoint k.
+lbm_status save_checkpoint(lbm_ctx* c, size_t k) {
+    while (c->ck.size() <= k) {
+        void* p = nullptr;
+        LBM_CUDA(c, cudaMalloc(&p, level_bytes(c)), "allocating a checkpoint");
+        c->ck.push_back(p);
+    }
+    LBM_CUDA(c, cudaMemcpyAsync(c->ck[k], c->f[c->cur], level_bytes(c), cudaMemcpyDeviceToDevice, c->stream),
+             "saving a checkpoint");
+    return LBM_OK;
+}
+
+lbm_status ensure_astage(lbm_ctx* c, size_t bytes) {
+    if (c->astage_bytes >= bytes) return LBM_OK;
+    cudaFree(c->d_astage);
+    c->d_astage = nullptr;
+    c->astage_bytes = 0;
+    LBM_CUDA(c, cudaMalloc(&c->d_astage, bytes), "allocating the adjoint staging buffer");
+    c->astage_bytes = bytes;
+    return LBM_OK;
+}
+
+// cuTensorMapEncodeTiled through the runtime's driver entry point (no link
+// against the driver library).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+    static EncodeTiledFn fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiledFn>(p);
+        cudaGetLastError();
+    }
+    return fn;
+}
+
+// 3D map (x: pitch columns, y: ny + 2 rows, z: 9 planes) of one FP32 level.
+bool make_tmap(CUtensorMap* m, void* base, const lbm_ctx& c) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) return false;
+    int bx = 0, by = 0;
+    tile_box_dims(&bx, &by);
+    const cuuint64_t dims[3] = {(cuuint64_t)c.pitch, (cuuint64_t)(c.ny + 2), 9};
+    const cuuint64_t strides[2] = {(cuuint64_t)c.pitch * 4, (cuuint64_t)c.plane * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 9};
+    const cuuint32_t es[3] = {1, 1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 struct CkptHeader {
     char magic[8];
     int nx, ny, prec, esize;
@@ -356,7 +432,7 @@ lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx
     c->diss = *diss;
     for (int k = 0; k < 4; ++k) c->bc[k] = bc[k];
     c->stream = static_cast<cudaStream_t>(stream);
-    if (prec == LBM_FP64) c->cfg.variant = STEP_SIMPLE;
+    if (prec == LBM_FP64) c->cfg = StepConfig{STEP_SIMPLE, 0, 0, 0};
     c->md = build_model(*c);
     c->mf = cast_model<float>(c->md);
     c->gd = build_grid<double>(*c, c->md);
@@ -378,6 +454,9 @@ lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx
         lbm_destroy(c);
         return r;
     }
+    if (c->prec != LBM_FP64)
+        c->tmap_ok = make_tmap(&c->tmap[0], c->f[0], *c) && make_tmap(&c->tmap[1], c->f[1], *c);
+    if (c->prec != LBM_FP64 && !c->tmap_ok) c->cfg = StepConfig{STEP_VEC, 4, 0, 0};
     *out = c;
     return LBM_OK;
 }
@@ -394,6 +473,13 @@ void lbm_destroy(lbm_ctx* c) {
     cudaFree(c->d_sums);
     cudaFreeHost(c->h_sums);
     cudaFree(c->d_stage);
+    for (void* p : c->ck) cudaFree(p);
+    for (void* p : c->seg) cudaFree(p);
+    cudaFree(c->adj[0]);
+    cudaFree(c->adj[1]);
+    cudaFree(c->d_taup);
+    cudaFreeHost(c->h_taup);
+    cudaFree(c->d_astage);
     cudaGetLastError();
     delete c;
 }
@@ -410,6 +496,8 @@ lbm_status lbm_init(lbm_ctx* c, const void* rho, const void* ux, const void* uy,
         if ((s = device_view(c, in[k], fb, k * fb, &d[k])) != LBM_OK) return s;
     c->cur = 0;
     c->step = 0;
+    c->ck_every = 0;
+    c->ck_base = -1;
     LBM_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream), "clearing status");
     cudaError_t e = dispatch(c, [&](auto tag, auto) {
         using S = decltype(tag);
@@ -430,6 +518,7 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
     if (n < 0) return fail(c, LBM_E_INVAL, "lbm_step: n must be >= 0");
     if (!c->ready) return fail(c, LBM_E_STATE, "lbm_step before lbm_init / lbm_set_f / lbm_load");
     for (int k = 0; k < n; ++k) {
+        c->cfg.tmap = c->tmap_ok ? &c->tmap[c->cur] : nullptr;
         cudaError_t e = dispatch(c, [&](auto tag, auto tm) {
             using S = decltype(tag);
             constexpr int TM = decltype(tm)::value;
@@ -439,6 +528,11 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
         if (e != cudaSuccess) return cuda_fail(c, e, "lbm_step");
         c->cur ^= 1;
         c->step += 1;
+        if (c->ck_every > 0 && (c->step - c->ck_base) % c->ck_every == 0) {
+            const size_t k = (size_t)((c->step - c->ck_base) / c->ck_every);
+            lbm_status r = save_checkpoint(c, k);
+            if (r != LBM_OK) return r;
+        }
     }
     return LBM_OK;
 }
@@ -547,17 +641,219 @@ lbm_status lbm_set_f(lbm_ctx* c, const void* src, long long step) {
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_set_f");
     c->step = step;
     c->ready = true;
+    c->ck_every = 0;
+    c->ck_base = -1;
     return LBM_OK;
 }
 
 long long lbm_step_count(const lbm_ctx* c) { return c ? c->step : -1; }
 
+lbm_status lbm_record(lbm_ctx* c, int every) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (every < 0) return fail(c, LBM_E_INVAL, "lbm_record: every must be >= 0");
+    if (!c->ready) return fail(c, LBM_E_STATE, "lbm_record before lbm_init");
+    c->ck_every = every;
+    c->ck_base = every > 0 ? c->step : -1;
+    if (every == 0) return LBM_OK;
+    return save_checkpoint(c, 0);
+}
+
+lbm_status lbm_adjoint_seed(lbm_ctx* c, const void* qr, const void* qx, const void* qy, const void* qT,
+                            void* abar) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!abar) return fail(c, LBM_E_INVAL, "lbm_adjoint_seed: abar must not be NULL");
+    if (!c->ready) return fail(c, LBM_E_STATE, "lbm_adjoint_seed before lbm_init");
+    const size_t fb = nodes(c) * c->esize;
+    if ((s = ensure_astage(c, 13 * fb)) != LBM_OK) return s;
+    const void* in[4] = {qr, qx, qy, qT};
+    const void* d[4];
+    for (int k = 0; k < 4; ++k) {
+        if (!in[k] || is_device_ptr(in[k])) {
+            d[k] = in[k];
+        } else {
+            char* dst = static_cast<char*>(c->d_astage) + (9 + k) * fb;
+            LBM_CUDA(c, cudaMemcpyAsync(dst, in[k], fb, cudaMemcpyHostToDevice, c->stream), "copying host qbar");
+            d[k] = dst;
+        }
+    }
+    const bool dev_out = is_device_ptr(abar);
+    void* out = dev_out ? abar : c->d_astage;
+    cudaError_t e = dispatch(c, [&](auto tag, auto tm) {
+        using S = decltype(tag);
+        constexpr int TM = decltype(tm)::value;
+        return launch_moments_vjp<S, TM>(static_cast<const S*>(c->f[c->cur]), (const S*)d[0], (const S*)d[1],
+                                         (const S*)d[2], (const S*)d[3], (S*)out, model_of<S>(c), grid_of<S>(c),
+                                         c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_adjoint_seed");
+    if (!dev_out) {
+        LBM_CUDA(c, cudaMemcpyAsync(abar, c->d_astage, 9 * fb, cudaMemcpyDeviceToHost, c->stream), "copying abar out");
+        LBM_CUDA(c, cudaStreamSynchronize(c->stream), "synchronising the stream");
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_adjoint_step(lbm_ctx* c, int n, void* abar, double* dL_dtau) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!abar || n < 0) return fail(c, LBM_E_INVAL, "lbm_adjoint_step: abar must not be NULL, n >= 0");
+    if (c->ck_every <= 0) return fail(c, LBM_E_STATE, "lbm_adjoint_step needs lbm_record first");
+    if (c->step - n < c->ck_base)
+        return fail(c, LBM_E_INVAL, "lbm_adjoint_step: only %lld steps recorded before the current level",
+                    c->step - c->ck_base);
+    if (n == 0) return LBM_OK;
+    const size_t fb = nodes(c) * c->esize, lb = level_bytes(c);
+    for (int k = 0; k < 2; ++k)
+        if (!c->adj[k]) {
+            LBM_CUDA(c, cudaMalloc(&c->adj[k], lb), "allocating adjoint levels");
+            LBM_CUDA(c, cudaMemsetAsync(c->adj[k], 0, lb, c->stream), "clearing adjoint levels");
+        }
+    while ((int)c->seg.size() < c->ck_every) {
+        void* p = nullptr;
+        LBM_CUDA(c, cudaMalloc(&p, lb), "allocating segment levels");
+        c->seg.push_back(p);
+    }
+    const int np = c->prec == LBM_FP64 ? adjoint_partials(c->gd) : adjoint_partials(c->gf);
+    if (c->ntaup < np) {
+        cudaFree(c->d_taup);
+        cudaFreeHost(c->h_taup);
+        c->d_taup = nullptr;
+        c->h_taup = nullptr;
+        LBM_CUDA(c, cudaMalloc((void**)&c->d_taup, sizeof(double) * np), "allocating tau partials");
+        LBM_CUDA(c, cudaMallocHost((void**)&c->h_taup, sizeof(double) * np), "allocating tau partials");
+        c->ntaup = np;
+    }
+    LBM_CUDA(c, cudaMemsetAsync(c->d_taup, 0, sizeof(double) * np, c->stream), "clearing tau partials");
+    // bring the caller's adjoint (dense) into adj[0]
+    const bool dev = is_device_ptr(abar);
+    if (!dev) {
+        if ((s = ensure_astage(c, 13 * fb)) != LBM_OK) return s;
+        LBM_CUDA(c, cudaMemcpyAsync(c->d_astage, abar, 9 * fb, cudaMemcpyHostToDevice, c->stream), "copying abar in");
+    }
+    const void* dense_in = dev ? abar : c->d_astage;
+    cudaError_t e = dispatch(c, [&](auto tag, auto) {
+        using S = decltype(tag);
+        return launch_unpack<S>(static_cast<S*>(c->adj[0]), (const S*)dense_in, grid_of<S>(c), c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_adjoint_step: unpacking abar");
+    StepConfig rcfg = c->cfg;  // recomputation writes segment buffers, which have no tensor maps
+    if (rcfg.variant == STEP_TILE) rcfg = StepConfig{STEP_SIMPLE, 0, 0, 0};
+    int ac = 0;
+    long long L = c->step;
+    const long long target = c->step - n;
+    long long c0 = L;
+    while (L > target) {
+        const long long k = (L - 1 - c->ck_base) / c->ck_every;
+        c0 = c->ck_base + k * c->ck_every;
+        const long long lo = c0 > target ? c0 : target;
+        LBM_CUDA(c, cudaMemcpyAsync(c->seg[0], c->ck[(size_t)k], lb, cudaMemcpyDeviceToDevice, c->stream),
+                 "restoring a checkpoint");
+        for (long long l = c0; l < L - 1; ++l) {
+            e = dispatch(c, [&](auto tag, auto tm) {
+                using S = decltype(tag);
+                constexpr int TM = decltype(tm)::value;
+                return launch_step<S, TM>(static_cast<const S*>(c->seg[(size_t)(l - c0)]),
+                                          static_cast<S*>(c->seg[(size_t)(l - c0 + 1)]), model_of<S>(c),
+                                          grid_of<S>(c), l, c->d_status, c->stream, rcfg);
+            });
+            if (e != cudaSuccess) return cuda_fail(c, e, "lbm_adjoint_step: recomputing");
+        }
+        for (long long l = L - 1; l >= lo; --l) {
+            e = dispatch(c, [&](auto tag, auto tm) {
+                using S = decltype(tag);
+                constexpr int TM = decltype(tm)::value;
+                return launch_adjoint<S, TM>(static_cast<const S*>(c->seg[(size_t)(l - c0)]),
+                                             static_cast<const S*>(c->adj[ac]), static_cast<S*>(c->adj[ac ^ 1]),
+                                             model_of<S>(c), grid_of<S>(c), l, c->d_taup, c->stream);
+            });
+            if (e != cudaSuccess) return cuda_fail(c, e, "lbm_adjoint_step");
+            ac ^= 1;
+        }
+        L = lo;
+    }
+    // the forward state moves back to level `target`
+    LBM_CUDA(c, cudaMemcpyAsync(c->f[c->cur], c->seg[(size_t)(target - c0)], lb, cudaMemcpyDeviceToDevice,
+                                c->stream),
+             "restoring the forward level");
+    c->step = target;
+    void* dense_out = dev ? abar : c->d_astage;
+    e = dispatch(c, [&](auto tag, auto) {
+        using S = decltype(tag);
+        return launch_pack<S>(static_cast<const S*>(c->adj[ac]), (S*)dense_out, grid_of<S>(c), c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_adjoint_step: packing abar");
+    if (!dev)
+        LBM_CUDA(c, cudaMemcpyAsync(abar, c->d_astage, 9 * fb, cudaMemcpyDeviceToHost, c->stream), "copying abar out");
+    LBM_CUDA(c, cudaMemcpyAsync(c->h_taup, c->d_taup, sizeof(double) * np, cudaMemcpyDeviceToHost, c->stream),
+             "copying tau partials");
+    LBM_CUDA(c, cudaStreamSynchronize(c->stream), "synchronising the stream");
+    if (dL_dtau) {
+        double t = 0.0;
+        for (int b = 0; b < np; ++b) t += c->h_taup[b];
+        *dL_dtau += -(c->dt / (c->tau * c->tau)) * t;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_feq_vjp(lbm_ctx* c, const void* rho, const void* ux, const void* uy, const void* T,
+                       const void* abar, void* grho, void* gux, void* guy, void* gT) {
+    lbm_status s = enter(c);
+    if (s != LBM_OK) return s;
+    if (!rho || !ux || !uy || !T || !abar) return fail(c, LBM_E_INVAL, "lbm_feq_vjp: NULL input");
+    const size_t fb = nodes(c) * c->esize;
+    if ((s = ensure_astage(c, 17 * fb)) != LBM_OK) return s;
+    char* st = static_cast<char*>(c->d_astage);
+    const void* in[5] = {rho, ux, uy, T, abar};
+    const size_t sz[5] = {fb, fb, fb, fb, 9 * fb};
+    const size_t off[5] = {0, fb, 2 * fb, 3 * fb, 4 * fb};
+    const void* d[5];
+    for (int k = 0; k < 5; ++k) {
+        if (is_device_ptr(in[k])) {
+            d[k] = in[k];
+        } else {
+            LBM_CUDA(c, cudaMemcpyAsync(st + off[k], in[k], sz[k], cudaMemcpyHostToDevice, c->stream), "copying inputs");
+            d[k] = st + off[k];
+        }
+    }
+    void* outs[4] = {grho, gux, guy, gT};
+    void* dout[4];
+    bool host_any = false;
+    for (int k = 0; k < 4; ++k) {
+        const bool h = outs[k] && !is_device_ptr(outs[k]);
+        host_any |= h;
+        dout[k] = !outs[k] ? nullptr : (h ? static_cast<void*>(st + (13 + k) * fb) : outs[k]);
+    }
+    cudaError_t e = dispatch(c, [&](auto tag, auto) {
+        using S = decltype(tag);
+        return launch_feq_vjp<S>((const S*)d[0], (const S*)d[1], (const S*)d[2], (const S*)d[3], (const S*)d[4],
+                                 (S*)dout[0], (S*)dout[1], (S*)dout[2], (S*)dout[3], model_of<S>(c),
+                                 (long long)nodes(c), c->stream);
+    });
+    if (e != cudaSuccess) return cuda_fail(c, e, "lbm_feq_vjp");
+    for (int k = 0; k < 4; ++k)
+        if (outs[k] && dout[k] != outs[k])
+            LBM_CUDA(c, cudaMemcpyAsync(outs[k], dout[k], fb, cudaMemcpyDeviceToHost, c->stream), "copying grads out");
+    if (host_any) LBM_CUDA(c, cudaStreamSynchronize(c->stream), "synchronising the stream");
+    return LBM_OK;
+}
+
 lbm_status lbm_set_launch(lbm_ctx* c, const lbm_launch* l) {
     lbm_status s = enter(c);
     if (s != LBM_OK) return s;
     if (!l) return fail(c, LBM_E_INVAL, "lbm_set_launch: launch must not be NULL");
-    if (l->variant != STEP_SIMPLE && l->variant != STEP_RING)
+    if (l->variant != STEP_SIMPLE && l->variant != STEP_RING && l->variant != STEP_VEC && l->variant != STEP_TILE)
         return fail(c, LBM_E_INVAL, "lbm_set_launch: unknown variant %d", l->variant);
+    if (l->variant == STEP_TILE) {
+        if (c->prec == LBM_FP64) return fail(c, LBM_E_INVAL, "lbm_set_launch: variant 3 is FP32-only");
+        if (!c->tmap_ok) return fail(c, LBM_E_INVAL, "lbm_set_launch: tensor maps unavailable on this driver");
+        if (l->grid < 0) return fail(c, LBM_E_INVAL, "lbm_set_launch: grid must be >= 0");
+    }
+    if (l->variant == STEP_VEC) {
+        if (c->prec == LBM_FP64) return fail(c, LBM_E_INVAL, "lbm_set_launch: variant 2 is FP32-only");
+        if (l->tx != 2 && l->tx != 4) return fail(c, LBM_E_INVAL, "lbm_set_launch: variant 2 needs tx = 2 or 4");
+    }
     if (l->variant == STEP_RING) {
         if (c->prec == LBM_FP64) return fail(c, LBM_E_INVAL, "lbm_set_launch: variant 1 is FP32-only");
         const bool ok = (l->tx == 256 && (l->ring == 4 || l->ring == 6)) || (l->tx == 128 && l->ring == 4);
@@ -589,6 +885,9 @@ lbm_status lbm_autotune(lbm_ctx* c, int steps, lbm_launch* best, double* ms, int
     int nc = 0;
     cands[nc++] = {STEP_SIMPLE, 0, 0, 0};
     if (c->prec != LBM_FP64) {
+        if (c->tmap_ok) cands[nc++] = {STEP_TILE, 0, 0, 0};
+        cands[nc++] = {STEP_VEC, 4, 0, 0};
+        cands[nc++] = {STEP_VEC, 2, 0, 0};
         cands[nc++] = {STEP_RING, 256, 4, 0};
         cands[nc++] = {STEP_RING, 256, 6, 0};
         cands[nc++] = {STEP_RING, 128, 4, 0};
@@ -598,6 +897,8 @@ lbm_status lbm_autotune(lbm_ctx* c, int steps, lbm_launch* best, double* ms, int
     if ((s = ensure_stage(c, bytes)) != LBM_OK) return s;
     const long long step0 = c->step;
     const StepConfig cfg0 = c->cfg;
+    const int every0 = c->ck_every;
+    c->ck_every = 0;  // trial steps must not overwrite recorded checkpoints
     cudaError_t e = dispatch(c, [&](auto tag, auto) {
         using S = decltype(tag);
         return launch_pack<S>(static_cast<const S*>(c->f[c->cur]), (S*)c->d_stage, grid_of<S>(c), c->stream);
@@ -642,6 +943,7 @@ lbm_status lbm_autotune(lbm_ctx* c, int steps, lbm_launch* best, double* ms, int
         return q;
     });
     c->step = step0;
+    c->ck_every = every0;
     *c->h_status = flags0;
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(c->d_status, c->h_status, sizeof(unsigned), cudaMemcpyHostToDevice, c->stream);
@@ -700,6 +1002,242 @@ lbm_status lbm_load(lbm_ctx* c, const void* buf, size_t bytes) {
         h.payload != (long long)(9 * nodes(c) * c->esize) || bytes < lbm_checkpoint_bytes(c) || h.step < 0)
         return fail(c, LBM_E_INVAL, "lbm_load: checkpoint does not match this context");
     return lbm_set_f(c, p + sizeof h, h.step);
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------------------ batch
+struct lbm_batch {
+    std::vector<lbm_ctx*> ctx;
+    lbm_precision prec = LBM_FP32;
+    cudaStream_t stream = nullptr;
+    int device = 0;
+    BatchProb* d_probs = nullptr;
+    int4* d_tiles = nullptr;
+    int ntiles = 0;
+    long long* d_level = nullptr;
+    unsigned* d_bar = nullptr;     // [0] arrivals, [1] generation
+    unsigned* d_status = nullptr;
+    unsigned* h_status = nullptr;
+    long long step = 0;
+    bool ready = false;
+    int grid = 0;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    int graph_n = -1;
+    int graph_state = 0;          // 1 captured and replayed, -1 capture failed
+    cudaStream_t gstream = nullptr;  // private stream the graph runs on
+    cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+    std::string err;
+};
+
+namespace {
+lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& msg) {
+    if (b) b->err = msg;
+    else g_create_err = msg;
+    return s;
+}
+
+cudaError_t batch_launch(lbm_batch* b, int n) {
+    auto go = [&](auto tm) {
+        constexpr int TM = decltype(tm)::value;
+        return launch_batch<TM>(b->d_probs, b->d_tiles, b->ntiles, n, b->d_level, b->d_bar, b->d_bar + 1,
+                                b->d_status, b->grid, b->stream);
+    };
+    switch (b->prec) {
+    case LBM_FP32_T64: return go(std::integral_constant<int, T_INT64>{});
+    case LBM_FP32_TDF: return go(std::integral_constant<int, T_DF>{});
+    default: return go(std::integral_constant<int, T_INT32>{});
+    }
+}
+}  // namespace
+
+extern "C" {
+
+void lbm_batch_destroy(lbm_batch* b) {
+    if (!b) return;
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    if (b->gstream) cudaStreamDestroy(b->gstream);
+    if (b->ev_in) cudaEventDestroy(b->ev_in);
+    if (b->ev_out) cudaEventDestroy(b->ev_out);
+    cudaFree(b->d_probs);
+    cudaFree(b->d_tiles);
+    cudaFree(b->d_level);
+    cudaFree(b->d_bar);
+    cudaFree(b->d_status);
+    cudaFreeHost(b->h_status);
+    for (lbm_ctx* c : b->ctx) lbm_destroy(c);
+    cudaGetLastError();
+    delete b;
+}
+
+const char* lbm_batch_last_error(const lbm_batch* b) { return b ? b->err.c_str() : g_create_err.c_str(); }
+
+lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision prec, void* stream,
+                            lbm_batch** out) {
+    if (!out) return bfail(nullptr, LBM_E_INVAL, "out must not be NULL");
+    *out = nullptr;
+    if (nprob < 1 || !probs) return bfail(nullptr, LBM_E_INVAL, "lbm_batch_create: need nprob >= 1 problems");
+    if (prec != LBM_FP32 && prec != LBM_FP32_T64 && prec != LBM_FP32_TDF)
+        return bfail(nullptr, LBM_E_INVAL, "lbm_batch_create: the batch runs the FP32 modes only");
+    lbm_batch* b = new lbm_batch();
+    b->prec = prec;
+    b->stream = static_cast<cudaStream_t>(stream);
+    cudaGetDevice(&b->device);
+    for (int p = 0; p < nprob; ++p) {
+        const lbm_problem& q = probs[p];
+        lbm_ctx* c = nullptr;
+        lbm_status s = lbm_create(q.nx, q.ny, q.b, q.tau, q.dt, q.dx, &q.dvm, &q.diss, q.bc, prec, stream, &c);
+        if (s != LBM_OK) {
+            std::string m = "problem " + std::to_string(p) + ": " + g_create_err;
+            lbm_batch_destroy(b);
+            return bfail(nullptr, s, m);
+        }
+        b->ctx.push_back(c);
+    }
+    int tw = 0, th = 0;
+    batch_tile_dims(&tw, &th);
+    std::vector<int4> tiles;
+    for (int p = 0; p < nprob; ++p)
+        for (int y0 = 0; y0 < probs[p].ny; y0 += th)
+            for (int x0 = 0; x0 < probs[p].nx; x0 += tw) tiles.push_back(make_int4(p, x0, y0, 0));
+    b->ntiles = (int)tiles.size();
+    std::vector<BatchProb> hp(nprob);
+    for (int p = 0; p < nprob; ++p) {
+        hp[p].f[0] = static_cast<float*>(b->ctx[p]->f[0]);
+        hp[p].f[1] = static_cast<float*>(b->ctx[p]->f[1]);
+        hp[p].M = b->ctx[p]->mf;
+        hp[p].G = b->ctx[p]->gf;
+    }
+    cudaError_t e = cudaMalloc((void**)&b->d_probs, sizeof(BatchProb) * nprob);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles, sizeof(int4) * tiles.size());
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_level, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_bar, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_status, sizeof(unsigned));
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_probs, hp.data(), sizeof(BatchProb) * nprob, cudaMemcpyHostToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice,
+                            b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), b->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(b->d_level, 0, sizeof(long long), b->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (e != cudaSuccess) {
+        std::string m = std::string("lbm_batch_create: ") + cudaGetErrorString(e);
+        lbm_batch_destroy(b);
+        return bfail(nullptr, e == cudaErrorMemoryAllocation ? LBM_E_NOMEM : LBM_E_CUDA, m);
+    }
+    int maxg = prec == LBM_FP32_T64 ? batch_max_grid<T_INT64>()
+               : prec == LBM_FP32_TDF ? batch_max_grid<T_DF>() : batch_max_grid<T_INT32>();
+    b->grid = maxg < b->ntiles ? maxg : b->ntiles;
+    *out = b;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_init(lbm_batch* b, const void* const* rho, const void* const* ux, const void* const* uy,
+                          const void* const* T) {
+    if (!b || !rho || !ux || !uy || !T) return bfail(b, LBM_E_INVAL, "lbm_batch_init: NULL argument");
+    for (size_t p = 0; p < b->ctx.size(); ++p) {
+        lbm_status s = lbm_init(b->ctx[p], rho[p], ux[p], uy[p], T[p]);
+        if (s != LBM_OK) return bfail(b, s, "problem " + std::to_string(p) + ": " + b->ctx[p]->err);
+    }
+    cudaSetDevice(b->device);
+    if (cudaMemsetAsync(b->d_level, 0, sizeof(long long), b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), b->stream) != cudaSuccess)
+        return bfail(b, LBM_E_CUDA, "lbm_batch_init: clearing the batch state failed");
+    b->step = 0;
+    b->ready = true;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_step(lbm_batch* b, int n) {
+    if (!b) return bfail(nullptr, LBM_E_INVAL, "NULL batch");
+    if (n < 0) return bfail(b, LBM_E_INVAL, "lbm_batch_step: n must be >= 0");
+    if (!b->ready) return bfail(b, LBM_E_STATE, "lbm_batch_step before lbm_batch_init");
+    if (n == 0) return LBM_OK;
+    cudaSetDevice(b->device);
+    cudaError_t e = cudaSuccess;
+    // One graph (a single cooperative kernel node) per step count, captured on
+    // a private stream and replayed there, ordered after and before the
+    // caller's stream by events; replays read the level from device memory,
+    // so one graph serves every call with the same n.
+    if (b->graph_state >= 0 && b->graph_n != n) {
+        if (b->exec) cudaGraphExecDestroy(b->exec);
+        if (b->graph) cudaGraphDestroy(b->graph);
+        b->exec = nullptr;
+        b->graph = nullptr;
+        b->graph_n = -1;
+        cudaStream_t keep = b->stream;
+        b->stream = b->gstream;  // batch_launch queues on b->stream
+        cudaGraph_t g = nullptr;
+        cudaError_t be = cudaStreamBeginCapture(b->gstream, cudaStreamCaptureModeThreadLocal);
+        cudaError_t le = be == cudaSuccess ? batch_launch(b, n) : be;
+        cudaError_t ce = be == cudaSuccess ? cudaStreamEndCapture(b->gstream, &g) : be;
+        cudaError_t ie = (le == cudaSuccess && ce == cudaSuccess && g) ? cudaGraphInstantiate(&b->exec, g, 0) : le;
+        b->stream = keep;
+        if (le == cudaSuccess && ce == cudaSuccess && ie == cudaSuccess && g) {
+            b->graph = g;
+            b->graph_n = n;
+            b->graph_state = 1;
+        } else {
+            if (g) cudaGraphDestroy(g);
+            b->exec = nullptr;
+            b->graph_state = -1;
+            b->err = std::string("graph capture of the batch launch failed (") +
+                     cudaGetErrorString(le != cudaSuccess ? le : (ce != cudaSuccess ? ce : ie)) +
+                     "); launching directly";
+        }
+        cudaGetLastError();
+    }
+    if (b->exec && b->graph_n == n) {
+        e = cudaEventRecord(b->ev_in, b->stream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->gstream, b->ev_in, 0);
+        if (e == cudaSuccess) e = cudaGraphLaunch(b->exec, b->gstream);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev_out, b->gstream);
+        if (e == cudaSuccess) e = cudaStreamWaitEvent(b->stream, b->ev_out, 0);
+    } else {
+        e = batch_launch(b, n);
+    }
+    if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string("lbm_batch_step: ") + cudaGetErrorString(e));
+    b->step += n;
+    for (lbm_ctx* c : b->ctx) {
+        c->step = b->step;
+        c->cur = (int)(b->step & 1);
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_sync(lbm_batch* b) {
+    if (!b) return bfail(nullptr, LBM_E_INVAL, "NULL batch");
+    cudaSetDevice(b->device);
+    if (cudaMemcpyAsync(b->h_status, b->d_status, sizeof(unsigned), cudaMemcpyDeviceToHost, b->stream) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(b->stream) != cudaSuccess)
+        return bfail(b, LBM_E_CUDA, "lbm_batch_sync: synchronising failed");
+    if (*b->h_status & ST_TIMEOUT) return bfail(b, LBM_E_TIMEOUT, "the batch grid barrier gave up");
+    if (*b->h_status & ST_NONPHYSICAL) return bfail(b, LBM_E_NONPHYSICAL, "a problem went non-physical");
+    return LBM_OK;
+}
+
+lbm_ctx* lbm_batch_problem(lbm_batch* b, int p) {
+    if (!b || p < 0 || p >= (int)b->ctx.size()) return nullptr;
+    return b->ctx[(size_t)p];
+}
+
+lbm_status lbm_batch_info(const lbm_batch* b, int* grid, int* ntiles, int* graph) {
+    if (!b) return LBM_E_INVAL;
+    if (grid) *grid = b->grid;
+    if (ntiles) *ntiles = b->ntiles;
+    if (graph) *graph = b->graph_state;
+    return LBM_OK;
 }
 
 }  // extern "C"

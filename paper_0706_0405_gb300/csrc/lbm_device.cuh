@@ -260,4 +260,134 @@ __device__ __forceinline__ void report(unsigned* status, unsigned bits) {
     if (any && (threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicOr(status, any);
 }
 
+// ------------------------------------------------- vectorised node group
+// One thread updates V x-adjacent nodes (ix0 .. ix0 + V - 1) of row iy,
+// reading the nine planes of its row segment and of the rows above and below
+// as V-wide vectors and the two x-neighbours at the ends as scalars; the
+// arithmetic per node is the explicitly rounded sequence of moments,
+// equilibrium and update, so every kernel built on it gives the same bits.
+// kCoherent: read through L2 only (data written earlier in the same kernel
+// by other CTAs); otherwise through the read-only path.  Returns the health
+// bits of the nodes inside the grid.
+template <int V>
+struct VecT;
+template <>
+struct VecT<2> {
+    using type = float2;
+};
+template <>
+struct VecT<4> {
+    using type = float4;
+};
+
+template <int V, bool kCoherent>
+__device__ __forceinline__ void load_vec(const float* p, float (&out)[V]) {
+    using T = typename VecT<V>::type;
+    const T v = kCoherent ? __ldcg(reinterpret_cast<const T*>(p)) : __ldg(reinterpret_cast<const T*>(p));
+    if constexpr (V == 2) {
+        out[0] = v.x;
+        out[1] = v.y;
+    } else {
+        out[0] = v.x;
+        out[1] = v.y;
+        out[2] = v.z;
+        out[3] = v.w;
+    }
+}
+
+template <int V>
+__device__ __forceinline__ void store_vec(float* p, const float (&o)[V]) {
+    using T = typename VecT<V>::type;
+    T v;
+    if constexpr (V == 2) {
+        v.x = o[0];
+        v.y = o[1];
+    } else {
+        v.x = o[0];
+        v.y = o[1];
+        v.z = o[2];
+        v.w = o[3];
+    }
+    *reinterpret_cast<T*>(p) = v;
+}
+
+template <bool kCoherent>
+__device__ __forceinline__ float load1(const float* p) {
+    return kCoherent ? __ldcg(p) : __ldg(p);
+}
+
+template <int V, int TM, bool kCoherent>
+__device__ __forceinline__ unsigned vec_group(const float* __restrict__ fin, float* __restrict__ fout,
+                                              const Model<float>& M, const Grid<float>& G, int ix0, int iy,
+                                              long long level) {
+    const int nvalid = min(V, G.nx - ix0);  // nodes of the segment inside the grid
+    const size_t pl = (size_t)G.plane;
+    const size_t c0 = cell(G, ix0, iy);     // 4 V-byte aligned: ix0 + PADX is a multiple of V
+    const float* in = fin + c0;
+
+    float C[9][V];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) load_vec<V, kCoherent>(in + i * pl, C[i]);
+
+    float acc[9][V];  // omega f^eq, the first term of the update
+    unsigned bits = 0;
+#pragma unroll
+    for (int k = 0; k < V; ++k) {
+        float f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = C[i][k];
+        float rho, ux, uy, T;
+        moments<float, TM>(f, M, rho, ux, uy, T);
+        if (k < nvalid) bits |= health(rho, ux, uy, T);
+        float fe[9];
+        equilibrium(M, rho, ux, uy, T, fe);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) acc[i][k] = mul_(M.omega, fe[i]);
+    }
+
+    float* out = fout + c0;
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const float* p = in + i * pl;
+        float Nn[V], Ss[V];
+        load_vec<V, kCoherent>(p + G.pitch, Nn);
+        load_vec<V, kCoherent>(p - G.pitch, Ss);
+        float row[V + 2];
+        row[0] = load1<kCoherent>(p - 1);
+        row[V + 1] = load1<kCoherent>(p + V);
+#pragma unroll
+        for (int k = 0; k < V; ++k) row[k + 1] = C[i][k];
+        float o[V];
+#pragma unroll
+        for (int k = 0; k < V; ++k) {
+            float a = fma_(M.w[i][0], row[k + 1], acc[i][k]);
+            a = fma_(M.w[i][1], row[k + 2], a);
+            a = fma_(M.w[i][2], row[k], a);
+            a = fma_(M.w[i][3], Nn[k], a);
+            o[k] = fma_(M.w[i][4], Ss[k], a);
+        }
+        if (nvalid == V) {
+            store_vec<V>(out + i * pl, o);
+        } else {
+#pragma unroll
+            for (int k = 0; k < V; ++k)
+                if (k < nvalid) out[i * pl + k] = o[k];
+        }
+    }
+    // Edge nodes also write the next level's ghost cells; their nine values
+    // are read back from what this thread just stored.
+    const bool edge_row = iy == 0 || iy == G.ny - 1;
+    if (edge_row || ix0 == 0 || ix0 + nvalid == G.nx) {
+        for (int k = 0; k < nvalid; ++k) {
+            const int ix = ix0 + k;
+            if (!(edge_row || ix == 0 || ix == G.nx - 1)) continue;
+            float v[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) v[i] = out[i * pl + k];
+            write_ghosts(G, fout, ix, iy, v, level + 1);
+        }
+    }
+    return bits;
+}
+
 }  // namespace lbm

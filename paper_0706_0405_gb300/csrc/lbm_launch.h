@@ -1,6 +1,7 @@
 // lbm_launch.h -- host-side launchers of the liblbm kernels (internal).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "lbm_device.cuh"
@@ -9,13 +10,17 @@ namespace lbm {
 
 // Kernel variant and launch shape of the step (chosen by the host, see
 // lbm_tune in lbm.h).
-enum StepVariant : int { STEP_SIMPLE = 0, STEP_RING = 1 };
+enum StepVariant : int { STEP_SIMPLE = 0, STEP_RING = 1, STEP_VEC = 2, STEP_TILE = 3 };
 struct StepConfig {
-    int variant = STEP_RING;  // FP64 always uses STEP_SIMPLE
-    int tx = 256;             // ring: columns per CTA (128 or 256)
-    int ring = 4;             // ring: shared-memory row slots (4 or 6; 4 when tx = 128)
-    int grid = 0;             // ring: CTAs (0 = SMs x resident CTAs per SM)
+    int variant = STEP_TILE;  // FP64 always uses STEP_SIMPLE
+    int tx = 0;               // ring: columns per CTA (128 or 256); vec: nodes per thread (2 or 4)
+    int ring = 0;             // ring: shared-memory row slots (4 or 6; 4 when tx = 128)
+    int grid = 0;             // ring, tile: CTAs (0 = SMs x resident CTAs per SM)
+    const CUtensorMap* tmap = nullptr;  // tile: tensor map of the input level
 };
+
+// Box of the tiled tensor copy of the tile kernel (x, y extent; 9 planes).
+void tile_box_dims(int* bx, int* by);
 
 // One step, level `level` in fin -> level + 1 in fout (ghosts included).
 template <typename S, int TM>
@@ -49,5 +54,34 @@ template <typename S>
 cudaError_t launch_pack(const S* f, S* dense, const Grid<S>& G, cudaStream_t st);
 template <typename S>
 cudaError_t launch_unpack(S* f, const S* dense, const Grid<S>& G, cudaStream_t st);
+
+// Adjoint (lbm_adjoint.cu).  a, abar: padded layout; taup: one FP64 slot per
+// block (adjoint_partials of them), accumulated across calls.
+template <typename S, int TM>
+cudaError_t launch_adjoint(const S* f, const S* a, S* abar, const Model<S>& M, const Grid<S>& G,
+                           long long level, double* taup, cudaStream_t st);
+template <typename S>
+int adjoint_partials(const Grid<S>& G);
+// Seed abar (dense 9 x n) = sum_m qbar_m dq_m/df at the level f; null qbar = 0.
+template <typename S, int TM>
+cudaError_t launch_moments_vjp(const S* f, const S* qr, const S* qx, const S* qy, const S* qT, S* abar,
+                               const Model<S>& M, const Grid<S>& G, cudaStream_t st);
+// Field gradient g = sum_i abar_i dF_i/dq at fields q (all dense, n nodes).
+template <typename S>
+cudaError_t launch_feq_vjp(const S* r, const S* ux, const S* uy, const S* T, const S* abar, S* gr, S* gx,
+                           S* gy, S* gT, const Model<S>& M, long long n, cudaStream_t st);
+
+// Batch (lbm_batch.cu): FP32 problems advanced by one cooperative launch.
+struct BatchProb {
+    float* f[2];  // the two levels; level k lives in f[k & 1]
+    Model<float> M;
+    Grid<float> G;
+};
+int batch_tile_dims(int* w, int* h);  // returns threads per CTA
+template <int TM>
+cudaError_t launch_batch(const BatchProb* probs, const int4* tiles, int ntiles, int nsteps, long long* level,
+                         unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid, cudaStream_t st);
+template <int TM>
+int batch_max_grid();
 
 }  // namespace lbm

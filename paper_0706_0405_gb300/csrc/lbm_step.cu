@@ -9,6 +9,10 @@
 
 namespace lbm {
 
+// Probes of an mbarrier before a wait gives up (each probe may suspend the
+// thread briefly); far beyond any copy latency.
+constexpr uint32_t kWaitLimit = 1u << 22;
+
 // One thread per node.  Each thread reads its node and the four star
 // neighbours of all nine populations (the neighbours come from L1/L2: the
 // same line serves the adjacent threads), computes the update in registers and
@@ -43,6 +47,160 @@ __global__ void __launch_bounds__(256) k_step_simple(const S* __restrict__ fin, 
         write_ghosts(G, fout, ix, iy, o, level + 1);
 }
 
+// ------------------------------------------------- FP32 vectorised kernel
+// Each thread updates V x-adjacent nodes of one row (V = 2 or 4), reading the
+// nine planes of its row segment and of the rows above and below as V-wide
+// vectors, and the two x-neighbours at the ends of the segment as scalars;
+// neighbours shared with the adjacent threads come from L1.  This cuts the
+// load and address instructions per node by V compared with one node per
+// thread, which was the limit of the thread-per-node kernel.  The arithmetic
+// per node is the same explicitly rounded sequence (moments, equilibrium,
+// update), so the levels are bit-identical to the other variants.
+template <int V, int TM>
+__global__ void __launch_bounds__(256) k_step_vec(const float* __restrict__ fin, float* __restrict__ fout,
+                                                  const Model<float> M, const Grid<float> G,
+                                                  long long level, unsigned* status) {
+    const int ix0 = (blockIdx.x * blockDim.x + threadIdx.x) * V;
+    const int iy = blockIdx.y * blockDim.y + threadIdx.y;
+    if (ix0 >= G.nx || iy >= G.ny) return;
+    report(status, vec_group<V, TM, false>(fin, fout, M, G, ix0, iy, level));
+}
+
+template <int V, int TM>
+cudaError_t launch_vec(const float* fin, float* fout, const Model<float>& M, const Grid<float>& G,
+                       long long level, unsigned* status, cudaStream_t st) {
+    dim3 block(32, 8);
+    const int groups = (G.nx + V - 1) / V;
+    dim3 grid((groups + block.x - 1) / block.x, (G.ny + block.y - 1) / block.y);
+    k_step_vec<V, TM><<<grid, block, 0, st>>>(fin, fout, M, G, level, status);
+    return cudaGetLastError();
+}
+
+// ------------------------------------------------------ FP32 TMA tile kernel
+// Persistent CTAs of 64 x 8 threads walk 64 x 8-node tiles.  For each tile
+// one thread issues a single tiled tensor copy of the 72 x 10 x 9 box (4
+// extra columns on each side for 16-byte alignment, one extra row above and
+// below, all nine planes) into one of two shared-memory stages; the next
+// tile's box is in flight while the current one is computed.  Each thread
+// then reads its node's five-point star from shared memory (no global loads,
+// no 64-bit address arithmetic), and writes its nine values.  Waits are
+// bounded: on give-up the CTA raises ST_TIMEOUT, drains, returns.
+constexpr int kTileX = 64, kTileY = 8;
+constexpr int kBoxX = kTileX + 8, kBoxY = kTileY + 2;
+constexpr int kBoxFloats = kBoxX * kBoxY * 9;
+constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages start on 128-byte boundaries
+constexpr size_t kTileSmem = 128 + sizeof(float) * 2 * kStageFloats + 2 * sizeof(uint64_t);
+
+template <int TM>
+__global__ void __launch_bounds__(kTileX * kTileY, 2)
+    k_step_tile(const __grid_constant__ CUtensorMap tmap, float* __restrict__ fout, const Model<float> M,
+                const Grid<float> G, long long level, unsigned* status, int tiles_x, int ntiles) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // tensor copies need a 128-byte aligned destination: align the base here
+    unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    float* box = reinterpret_cast<float*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(float) * 2 * kStageFloats);
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, tx = tid % kTileX, ty = tid / kTileX;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int tile, int stage) {
+        const int x0 = (tile % tiles_x) * kTileX, y0 = (tile / tiles_x) * kTileY;
+        mbar_arrive_expect_tx(&bar[stage], (uint32_t)(sizeof(float) * kBoxFloats));
+        // array column x0 is interior column x0 - 4; array row y0 is interior row y0 - 1
+        tma_load_3d(box + stage * kStageFloats, &tmap, x0, y0, 0, &bar[stage]);
+    };
+    auto wait = [&](int k) { return mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), kWaitLimit); };
+    int issued = -1, waited = -1;  // local tile indices (same in every thread)
+    if (blockIdx.x < ntiles) {
+        if (tid == 0) issue(blockIdx.x, 0);
+        issued = 0;
+    }
+    const size_t pl = (size_t)G.plane;
+    unsigned bits = 0;
+    for (int k = 0;; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        __syncthreads();  // every thread is done with the stage of tile k - 1
+        if (abort_flag) {
+            for (int j = waited + 1; j <= issued; ++j) wait(j);
+            if (tid == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
+        if (t + (int)gridDim.x < ntiles) {
+            if (tid == 0) issue(t + gridDim.x, (k + 1) & 1);
+            issued = k + 1;
+        }
+        if (!wait(k)) {
+            abort_flag = 1;
+            continue;
+        }
+        waited = k;
+        const int ix = (t % tiles_x) * kTileX + tx, iy = (t / tiles_x) * kTileY + ty;
+        if (ix >= G.nx || iy >= G.ny) continue;
+        const float* b = box + (k & 1) * kStageFloats + (ty + 1) * kBoxX + (tx + 4);
+        constexpr int P = kBoxX * kBoxY;  // floats per plane in the box
+        float f[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) f[i] = b[i * P];
+        float rho, ux, uy, T;
+        moments<float, TM>(f, M, rho, ux, uy, T);
+        bits |= health(rho, ux, uy, T);
+        float fe[9], o[9];
+        equilibrium(M, rho, ux, uy, T, fe);
+#pragma unroll
+        for (int i = 0; i < 9; ++i)
+            o[i] = update(M, i, fe[i], f[i], b[i * P + 1], b[i * P - 1], b[i * P + kBoxX], b[i * P - kBoxX]);
+        const size_t c = cell(G, ix, iy);
+#pragma unroll
+        for (int i = 0; i < 9; ++i) fout[i * pl + c] = o[i];
+        if (ix == 0 || iy == 0 || ix == G.nx - 1 || iy == G.ny - 1) write_ghosts(G, fout, ix, iy, o, level + 1);
+    }
+    __syncthreads();
+    if (abort_flag) {  // a wait of the last tile gave up
+        for (int j = waited + 1; j <= issued; ++j) wait(j);
+        if (tid == 0) atomicOr(status, ST_TIMEOUT);
+        return;
+    }
+    report(status, bits);
+}
+
+void tile_box_dims(int* bx, int* by) {
+    *bx = kBoxX;
+    *by = kBoxY;
+}
+
+template <int TM>
+cudaError_t launch_tile(const CUtensorMap& tmap, float* fout, const Model<float>& M, const Grid<float>& G,
+                        long long level, unsigned* status, int grid_hint, cudaStream_t st) {
+    constexpr size_t smem = kTileSmem;
+    auto kern = k_step_tile<TM>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    const int tiles_x = (G.nx + kTileX - 1) / kTileX;
+    const int ntiles = tiles_x * ((G.ny + kTileY - 1) / kTileY);
+    int grid = grid_hint;
+    if (grid <= 0) {
+        static int full_wave = 0;
+        if (full_wave == 0) {
+            int dev = 0, sms = 0, per_sm = 0;
+            cudaGetDevice(&dev);
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileX * kTileY, smem);
+            full_wave = sms * (per_sm > 0 ? per_sm : 1);
+        }
+        grid = full_wave;
+    }
+    if (grid > ntiles) grid = ntiles;
+    kern<<<grid, kTileX * kTileY, smem, st>>>(tmap, fout, M, G, level, status, tiles_x, ntiles);
+    return cudaGetLastError();
+}
+
 // ------------------------------------------------------ FP32 ring kernel
 // Each CTA owns TX consecutive columns ("strip") and marches up a contiguous
 // run of rows of that strip (the runs of all CTAs tile the flattened
@@ -54,7 +212,6 @@ __global__ void __launch_bounds__(256) k_step_simple(const S* __restrict__ fin, 
 // neighbours of row y from the slot.  Every wait is bounded: on give-up the
 // CTA raises ST_TIMEOUT, drains its copies in flight (again bounded) and
 // returns.
-constexpr uint32_t kWaitLimit = 1u << 22;
 
 template <int TX, int R, int TM>
 __global__ void __launch_bounds__(TX, 2)
@@ -223,6 +380,12 @@ template <typename S, int TM>
 cudaError_t launch_step(const S* fin, S* fout, const Model<S>& M, const Grid<S>& G,
                         long long level, unsigned* status, cudaStream_t st, const StepConfig& cfg) {
     if constexpr (sizeof(S) == 4) {
+        if (cfg.variant == STEP_TILE && cfg.tmap != nullptr)
+            return launch_tile<TM>(*cfg.tmap, fout, M, G, level, status, cfg.grid, st);
+        if (cfg.variant == STEP_VEC) {
+            if (cfg.tx == 2) return launch_vec<2, TM>(fin, fout, M, G, level, status, st);
+            return launch_vec<4, TM>(fin, fout, M, G, level, status, st);
+        }
         if (cfg.variant == STEP_RING) {
             if (cfg.tx == 128) return launch_ring<128, 4, TM>(fin, fout, M, G, level, status, cfg.grid, st);
             if (cfg.ring == 6) return launch_ring<256, 6, TM>(fin, fout, M, G, level, status, cfg.grid, st);

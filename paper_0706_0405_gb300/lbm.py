@@ -27,7 +27,11 @@ BC_KINDS = {"periodic": 0, "outflow": 1, "dirichlet": 2, "reflect": 3}
 EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init", "lbm_step", "lbm_moments",
            "lbm_conservation", "lbm_sync", "lbm_get_f", "lbm_set_f", "lbm_step_count",
            "lbm_checkpoint_bytes", "lbm_save", "lbm_load", "lbm_version", "lbm_health",
-           "lbm_set_launch", "lbm_get_launch", "lbm_autotune", "lbm_conservation_noalloc")
+           "lbm_set_launch", "lbm_get_launch", "lbm_autotune", "lbm_conservation_noalloc",
+           "lbm_record", "lbm_adjoint_seed", "lbm_adjoint_step", "lbm_feq_vjp",
+           "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_init",
+           "lbm_batch_step", "lbm_batch_sync", "lbm_batch_problem", "lbm_batch_info",
+           "lbm_probe_rates")
 LBM_FLAG_NONPHYSICAL, LBM_FLAG_TIMEOUT, LBM_FLAG_T_NONPOSITIVE = 1, 2, 4
 
 
@@ -49,6 +53,12 @@ class lbm_dvm(ctypes.Structure):
 
 class lbm_dissipation(ctypes.Structure):
     _fields_ = [("beta", ctypes.c_double), ("lambda_", ctypes.c_double * 9)]
+
+
+class lbm_problem(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("b", ctypes.c_double),
+                ("tau", ctypes.c_double), ("dt", ctypes.c_double), ("dx", ctypes.c_double),
+                ("dvm", lbm_dvm), ("diss", lbm_dissipation), ("bc", lbm_bc * 4)]
 
 
 class lbm_launch(ctypes.Structure):
@@ -95,6 +105,22 @@ def load():
         "lbm_load": ([ctx, _VP, ctypes.c_size_t], ctypes.c_int),
         "lbm_version": ([], ctypes.c_char_p),
         "lbm_set_launch": ([ctx, ctypes.POINTER(lbm_launch)], ctypes.c_int),
+        "lbm_record": ([ctx, ctypes.c_int], ctypes.c_int),
+        "lbm_probe_rates": ([ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+                            ctypes.c_int),
+        "lbm_batch_create": ([ctypes.c_int, ctypes.POINTER(lbm_problem), ctypes.c_int, _VP,
+                              ctypes.POINTER(_VP)], ctypes.c_int),
+        "lbm_batch_destroy": ([_VP], None),
+        "lbm_batch_last_error": ([_VP], ctypes.c_char_p),
+        "lbm_batch_init": ([_VP] + [ctypes.POINTER(_VP)] * 4, ctypes.c_int),
+        "lbm_batch_step": ([_VP, ctypes.c_int], ctypes.c_int),
+        "lbm_batch_sync": ([_VP], ctypes.c_int),
+        "lbm_batch_problem": ([_VP, ctypes.c_int], _VP),
+        "lbm_batch_info": ([_VP, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                            ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
+        "lbm_adjoint_seed": ([ctx, _VP, _VP, _VP, _VP, _VP], ctypes.c_int),
+        "lbm_adjoint_step": ([ctx, ctypes.c_int, _VP, ctypes.POINTER(ctypes.c_double)], ctypes.c_int),
+        "lbm_feq_vjp": ([ctx] + [_VP] * 9, ctypes.c_int),
         "lbm_conservation_noalloc": ([_VP, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.POINTER(lbm_dvm), ctypes.POINTER(ctypes.c_double), _VP],
                                      ctypes.c_int),
@@ -224,6 +250,26 @@ def lbm_conservation_noalloc(f, nx, ny, prec, dvm, stream=None):
     return np.array(out[:])
 
 
+def lbm_record(ctx, every):
+    return _check(ctx, load().lbm_record(ctx, int(every)))
+
+
+def lbm_adjoint_seed(ctx, qr, qx, qy, qT, abar):
+    return _check(ctx, load().lbm_adjoint_seed(ctx, _ptr(qr), _ptr(qx), _ptr(qy), _ptr(qT), _ptr(abar)))
+
+
+def lbm_adjoint_step(ctx, n, abar):
+    """Returns the tau derivative of the n steps."""
+    d = ctypes.c_double(0.0)
+    _check(ctx, load().lbm_adjoint_step(ctx, int(n), _ptr(abar), ctypes.byref(d)))
+    return float(d.value)
+
+
+def lbm_feq_vjp(ctx, rho, ux, uy, T, abar, g_rho, g_ux, g_uy, g_T):
+    return _check(ctx, load().lbm_feq_vjp(ctx, _ptr(rho), _ptr(ux), _ptr(uy), _ptr(T), _ptr(abar),
+                                          _ptr(g_rho), _ptr(g_ux), _ptr(g_uy), _ptr(g_T)))
+
+
 def lbm_set_launch(ctx, variant, tx=256, ring=4, grid=0):
     return _check(ctx, load().lbm_set_launch(ctx, ctypes.byref(lbm_launch(variant, tx, ring, grid))))
 
@@ -243,6 +289,62 @@ def lbm_autotune(ctx, steps=20):
     return best.as_tuple(), list(ms[: n.value])
 
 
+def lbm_probe_rates():
+    """(FP64 TFLOP/s, FP32 TFLOP/s) of the current device."""
+    a, b = ctypes.c_double(), ctypes.c_double()
+    st = load().lbm_probe_rates(ctypes.byref(a), ctypes.byref(b))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_probe_rates failed")
+    return a.value, b.value
+
+
+def _bcheck(b, status):
+    if status != LBM_OK:
+        raise LbmError(status, load().lbm_batch_last_error(b).decode())
+    return status
+
+
+def lbm_batch_create(problems, prec, stream=None):
+    arr = (lbm_problem * len(problems))(*problems)
+    out = _VP()
+    st = load().lbm_batch_create(len(problems), arr,
+                                 PRECISIONS.get(prec, prec) if isinstance(prec, str) else int(prec),
+                                 _ptr(stream), ctypes.byref(out))
+    _bcheck(None, st)
+    return out.value
+
+
+def lbm_batch_destroy(b):
+    load().lbm_batch_destroy(b)
+
+
+def lbm_batch_last_error(b=None):
+    return load().lbm_batch_last_error(b).decode()
+
+
+def lbm_batch_init(b, rho, ux, uy, T):
+    arrs = [(_VP * len(x))(*[_ptr(a) for a in x]) for x in (rho, ux, uy, T)]
+    return _bcheck(b, load().lbm_batch_init(b, *arrs))
+
+
+def lbm_batch_step(b, n):
+    return _bcheck(b, load().lbm_batch_step(b, int(n)))
+
+
+def lbm_batch_sync(b):
+    return _bcheck(b, load().lbm_batch_sync(b))
+
+
+def lbm_batch_problem(b, p):
+    return load().lbm_batch_problem(b, int(p))
+
+
+def lbm_batch_info(b):
+    g, t, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _bcheck(b, load().lbm_batch_info(b, ctypes.byref(g), ctypes.byref(t), ctypes.byref(gr)))
+    return g.value, t.value, gr.value
+
+
 # ------------------------------------------------------------ convenience
 
 def make_bc(side) -> lbm_bc:
@@ -255,6 +357,85 @@ def make_bc(side) -> lbm_bc:
         b.state_lo[q] = float(side.state_lo[q])
         b.state_hi[q] = float(side.state_hi[q])
     return b
+
+
+def make_problem(p) -> lbm_problem:
+    """lbm_problem of a problem description (attributes of workloads.Problem)."""
+    q = lbm_problem()
+    q.nx, q.ny = int(p.nx), int(p.ny)
+    q.b, q.tau, q.dt, q.dx = float(p.b), float(p.tau), float(p.dt), float(p.dx)
+    q.dvm = lbm_dvm(p.c1, p.c2, p.eta0)
+    q.diss.beta = float(p.beta)
+    for i in range(9):
+        q.diss.lambda_[i] = float(p.lam[i])
+    for k in range(4):
+        q.bc[k] = make_bc(p.sides[k])
+    return q
+
+
+class Batch:
+    """One lbm_batch for a list of problem descriptions (FP32 modes)."""
+
+    def __init__(self, problems, precision: str = "fp32", stream=None):
+        import torch
+        self.problems = list(problems)
+        self.precision = precision
+        if stream is None:
+            stream = torch.cuda.current_stream().cuda_stream
+        self.handle = lbm_batch_create([make_problem(p) for p in self.problems], precision, stream)
+
+    def close(self):
+        if self.handle:
+            lbm_batch_destroy(self.handle)
+            self.handle = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def init(self, fields):
+        """fields[p] = (rho, ux, uy, T) of problem p."""
+        import torch
+        ts = [[torch.as_tensor(np.ascontiguousarray(a, dtype=np.float32), device="cuda") for a in fl]
+              for fl in fields]
+        lbm_batch_init(self.handle, *[[t[q] for t in ts] for q in range(4)])
+        self._keep = ts
+        return self
+
+    def step(self, n: int):
+        lbm_batch_step(self.handle, n)
+        return self
+
+    def sync(self):
+        lbm_batch_sync(self.handle)
+
+    def info(self):
+        return lbm_batch_info(self.handle)
+
+    def moments(self, p: int):
+        import torch
+        prob = self.problems[p]
+        ctx = lbm_batch_problem(self.handle, p)
+        out = [torch.empty((prob.ny, prob.nx), dtype=torch.float32, device="cuda") for _ in range(4)]
+        lbm_moments(ctx, *out)
+        torch.cuda.synchronize()
+        return out
+
+    def get_f(self, p: int):
+        import torch
+        prob = self.problems[p]
+        out = torch.empty((9, prob.ny, prob.nx), dtype=torch.float32, device="cuda")
+        lbm_get_f(lbm_batch_problem(self.handle, p), out)
+        torch.cuda.synchronize()
+        return out
 
 
 class Lattice:

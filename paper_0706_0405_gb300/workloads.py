@@ -138,6 +138,29 @@ def mach3_2048x256(steps: int = 1000) -> Problem:
                    0.5, 4.0, 10.0, 6.0, alpha=0.05, steps=steps)
 
 
+def batch_riemann(count: int = 256, seed: int = 0, steps: int = 1000, ny: int = 4):
+    """Many Riemann tubes of uneven length, drawn from PCG64(seed):
+    nx = round(exp(U[ln 256, ln 4096])) cells on [0, 1] (dx = 1 / nx), ny
+    rows, diaphragm at 0.5; (rho, p)_L = (r, r) with r = exp(U[0, ln 1000]),
+    (rho, p)_R = (1, 1) (T = 1 on both sides), left velocity M sqrt(1.4) with
+    M ~ U[0, 30] (Mach M), right at rest.  DVM constants per tube:
+    c1 = max(3, 1.1 u_L + 2), c2 = 2.4 c1, eta0 = 1.2 c1, lambda = 2 x Eq. 13,
+    dt = 0.05 dx / c2, tau = dt (max|omega| = 1 at the left, right and star
+    states, checked by the tests)."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    L = np.round(np.exp(rng.uniform(math.log(256), math.log(4096), count))).astype(int)
+    r = np.exp(rng.uniform(0.0, math.log(1000.0), count))
+    M = rng.uniform(0.0, 30.0, count)
+    out = []
+    for k in range(count):
+        uL = float(M[k]) * math.sqrt(GAMMA_AIR)
+        c1 = max(3.0, 1.1 * uL + 2.0)
+        out.append(riemann(f"tube{k}_{L[k]}x{ny}", int(L[k]), ny, 1.0, (float(r[k]), uL, 0.0, float(r[k])),
+                           (1.0, 0.0, 0.0, 1.0), 0.5, c1, 2.4 * c1, 1.2 * c1, alpha=0.05, steps=steps,
+                           lam_scale=2.0))
+    return out
+
+
 # ------------------------------------------------------- double Mach reflection
 
 DMR_PRE = (1.4, 0.0, 0.0, 1.0)       # (rho, u, v, p) ahead of the shock

@@ -1,0 +1,62 @@
+"""The batched persistent launch (lbm_batch_*) against stepping each problem
+alone and against the oracle."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_0706_0405_gb300 import lbm
+from paper_0706_0405_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+def _subset():
+    probs = W.batch_riemann()
+    idx = [0, 3, 17, 42, 99, 128, 200, 255]
+    return [probs[k] for k in idx]
+
+
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tdf"])
+def test_batch_equals_problems_stepped_alone(prec):
+    probs = _subset()
+    fields = [W.initial_fields(p) for p in probs]
+    with lbm.Batch(probs, prec) as b:
+        b.init(fields).step(150).step(50)
+        b.sync()
+        grid, ntiles, graph = b.info()
+        got = [b.get_f(k).cpu().numpy() for k in range(len(probs))]
+    assert graph == 1 and ntiles > len(probs) and grid > 0
+    for p, fl, g in zip(probs, fields, got):
+        with lbm.Lattice(p, prec) as lat:
+            lat.init(*fl).step(200)
+            want = lat.get_f().cpu().numpy()
+        assert np.array_equal(g, want), p.name
+
+
+def test_batch_matches_oracle():
+    probs = W.batch_riemann()
+    pick = [5, 77, 180]
+    with lbm.Batch(probs, "fp32") as b:
+        b.init([W.initial_fields(p) for p in probs]).step(1000)
+        b.sync()
+        got = {k: [t.double().cpu().numpy() for t in b.moments(k)] for k in pick}
+    oracle.set_threads(oracle.max_threads())
+    for k in pick:
+        p = probs[k]
+        f = oracle.init(p, *W.initial_fields(p))
+        assert oracle.run(p, f, 1000) == 0
+        ref = oracle.fields(p, f)
+        for q in (0, 3):
+            l1 = np.sum(np.abs(got[k][q] - ref[q])) / np.sum(np.abs(ref[q]))
+            assert l1 <= 1e-3, (p.name, q, l1)
+
+
+def test_batch_argument_errors():
+    probs = _subset()[:2]
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.Batch(probs, "fp64")
+    assert ei.value.status == lbm.LBM_E_INVAL
+    with lbm.Batch(probs, "fp32") as b:
+        with pytest.raises(lbm.LbmError) as ei:
+            b.step(1)
+        assert ei.value.status == lbm.LBM_E_STATE

@@ -301,18 +301,23 @@ def test_step_before_init_is_a_state_error():
 
 # ---------------------------------------------------------- launch shapes
 
-SHAPES = [(0, 0, 0, 0), (1, 256, 4, 0), (1, 256, 6, 0), (1, 128, 4, 0), (1, 256, 4, 7),
-          (1, 128, 4, 1)]
+SHAPES = [(0, 0, 0, 0), (3, 0, 0, 0), (3, 0, 0, 5), (2, 4, 0, 0), (2, 2, 0, 0), (1, 256, 4, 0),
+          (1, 256, 6, 0), (1, 128, 4, 0), (1, 256, 4, 7), (1, 128, 4, 1)]
 
 
 @pytest.mark.parametrize("prec", FP32_MODES)
 @pytest.mark.parametrize("ny", [64, 37])
 def test_every_launch_shape_gives_the_same_bits(prec, ny):
-    """The thread-per-node kernel and every shape of the strip-marching ring
-    kernel (including a grid of 1 and 7 CTAs, and a grid whose width is not a
-    multiple of the strip width) do the same explicitly rounded arithmetic in
-    the same order, so their levels agree bit for bit, edges included."""
+    """The thread-per-node kernel, the TMA tile kernel (full wave and 5 CTAs),
+    the vectorised kernel (2 and 4 nodes per thread) and every shape of the
+    strip-marching ring kernel (including a grid of 1 and 7 CTAs), on a grid
+    whose width is not a multiple of any tile, vector or strip width, do the
+    same explicitly rounded arithmetic in the same order, so their levels
+    agree bit for bit, edges included."""
     p = W.dmr(ny).with_(nx=4 * ny + 3) if ny == 37 else W.dmr(ny)
+    if ny == 37:
+        p = p.with_(sides=(p.sides[0], W.Side("periodic"), p.sides[2], p.sides[3]))
+        p = p.with_(sides=(W.Side("periodic"),) + p.sides[1:])
     outs = []
     for shape in SHAPES:
         with lbm.Lattice(p, prec) as lat:
@@ -324,11 +329,12 @@ def test_every_launch_shape_gives_the_same_bits(prec, ny):
         assert np.array_equal(o, outs[0]), s
 
 
-def test_ring_matches_oracle_on_ragged_grid():
+@pytest.mark.parametrize("shape", [(3, 0, 0, 0), (1, 128, 4, 0), (2, 4, 0, 0), (2, 2, 0, 0)])
+def test_fp32_kernels_match_oracle_on_ragged_grid(shape):
     p = W.dmr(37).with_(nx=151, steps=120)
-    ref = oracle_run(p)[0]
+    ref = cached_oracle("dmr151x37", p)
     with lbm.Lattice(p, "fp32") as lat:
-        lbm.lbm_set_launch(lat.ctx, 1, 128, 4, 0)
+        lbm.lbm_set_launch(lat.ctx, *shape)
         lat.init(*W.initial_fields(p)).step(p.steps)
         g = [t.double().cpu().numpy() for t in lat.moments()]
     assert l1_rel(g[0], ref[0]) <= 1e-4 and l1_rel(g[3], ref[3]) <= 1e-4
@@ -342,7 +348,7 @@ def test_autotune_restores_state_and_picks_a_shape():
         best, ms = lbm.lbm_autotune(lat.ctx, 5)
         assert lat.step_count == 10
         assert np.array_equal(lat.get_f().cpu().numpy(), before)
-        assert len(ms) == 4 and all(m > 0 for m in ms)
+        assert len(ms) == 7 and all(m > 0 for m in ms)
         assert lbm.lbm_get_launch(lat.ctx) == best
     with lbm.Lattice(p, "fp64") as lat:
         with pytest.raises(lbm.LbmError):

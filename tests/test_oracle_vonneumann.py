@@ -148,3 +148,20 @@ def test_config_parameters_are_vetted(make):
     for st in states:
         g = vn.max_growth(st, p.b, p.c1, p.c2, p.eta0, p.dt, p.dx, p.tau, p.beta, np.array(p.lam))
         assert g <= 1.0 + 1e-9, (p.name, st, g)
+
+
+def test_batch_parameters_are_vetted():
+    """The per-tube constants of the batched workload keep max|omega| <= 1 at
+    the left, right and both star states (every 8th tube of the 256)."""
+    from oracle import gasdynamics as gd
+    probs = W.batch_riemann()
+    for p in probs[::8]:
+        L, R = p.setup["left"], p.setup["right"]
+        WL, WR = (L[0], L[1], L[0] * L[3]), (R[0], R[1], R[0] * R[3])
+        ps, us = gd.riemann_star(WL, WR, 1.4)
+        s = gd.riemann_sample(WL, WR, 1.4, [us - 1e-9, us + 1e-9])
+        states = [L, R, (s[0, 0], us, 0.0, s[2, 0] / s[0, 0]), (s[0, 1], us, 0.0, s[2, 1] / s[0, 1])]
+        for st in states:
+            g = vn.max_growth(st, p.b, p.c1, p.c2, p.eta0, p.dt, p.dx, p.tau, p.beta, np.array(p.lam),
+                              npts=16)
+            assert g <= 1.0 + 1e-9, (p.name, st, g)
