@@ -49,6 +49,8 @@ def parse():
     ap.add_argument("--ny", type=int, default=1024)
     ap.add_argument("--extras", type=int, default=1)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--case", default=None, choices=("dmr_step", "batch_step", "adjoint_step"),
+                    help="run one kernel's small case a few times (for a profiler) and exit")
     return ap.parse_args()
 
 
@@ -416,8 +418,44 @@ def reference_arm(args, world, budget_s=120.0):
             "e2e": {"value": value, "unit": "GLUPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 
+def profile_case(args):
+    """A few launches of one kernel on its benchmark workload, for ncu:
+    dmr_step: 3 steps of the 4096 x 1024 DMR (--precision); batch_step: one
+    persistent launch of 20 steps of the 256 tubes; adjoint_step: 20 adjoint
+    steps of the Mach-3 2048 x 256 tube (checkpoint every 10)."""
+    import torch
+    from paper_0706_0405_gb300 import lbm
+    from paper_0706_0405_gb300 import workloads as W
+    if args.case == "dmr_step":
+        p = W.dmr(args.ny)
+        with lbm.Lattice(p, args.precision) as lat:
+            lat.init(*W.initial_fields(p)).step(3)
+            lat.sync()
+    elif args.case == "batch_step":
+        probs = W.batch_riemann()
+        side = torch.cuda.Stream()
+        with lbm.Batch(probs, args.precision, stream=side.cuda_stream) as b:
+            b.init([W.initial_fields(q) for q in probs]).step(20)
+            b.sync()
+    else:
+        q = W.mach3_2048x256(steps=20)
+        with lbm.Lattice(q, args.precision) as la:
+            la.init(*W.initial_fields(q, seed=0, sigma=0.01))
+            lbm.lbm_record(la.ctx, 10)
+            la.step(20)
+            abar = torch.zeros((9, q.ny, q.nx), dtype=la.dtype, device="cuda")
+            lbm.lbm_adjoint_seed(la.ctx, torch.ones((q.ny, q.nx), dtype=la.dtype, device="cuda"),
+                                 None, None, None, abar)
+            lbm.lbm_adjoint_step(la.ctx, 20, abar)
+    torch.cuda.synchronize()
+    print(json.dumps({"case": args.case, "precision": args.precision, "ok": True}))
+
+
 def main():
     args = parse()
+    if args.case:
+        profile_case(args)
+        return
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
     dist = None

@@ -292,8 +292,8 @@ lbm_status lbm_conservation_noalloc(const void* f, int nx, int ny, lbm_precision
 /* --------------------------------------------------------------- batch
  * Many independent problems (each with its own grid, constants and boundary
  * kinds) advanced together by one persistent cooperative kernel launch per
- * lbm_batch_step call: every CTA walks a static share of the list of
- * (problem, 256 x 4 node tile) pairs each step and a bounded grid barrier
+ * lbm_batch_step call: every CTA walks a contiguous share of the list of
+ * (problem, 64 x 4 node tile) pairs each step and a bounded grid barrier
  * separates the steps (LBM_E_TIMEOUT if it gives up).  The launch is captured
  * once per step count into a CUDA graph on a stream private to the batch and
  * replayed there, ordered after the batch's stream by events (so the legacy

@@ -129,3 +129,34 @@ def moving_shock(rho1, p1, mach, gamma):
     s = mach * sound_speed(rho1, p1, gamma)
     rho2, w2, p2 = normal_shock(rho1, s, p1, gamma)
     return rho2, s - w2, p2, s
+
+
+def oblique_shock_for_turn(rho1, ux1, uy1, p1, turn, gamma, strong=False):
+    """Stationary oblique shock that turns the flow (ux1, uy1) by the angle
+    `turn` (radians, counter-clockwise positive) and its downstream state.
+    The shock angle beta (between the upstream velocity and the shock) solves
+    tan(turn) = 2 cot(beta) (M^2 sin^2 beta - 1) / (M^2 (gamma + cos 2 beta) + 2);
+    the weak root is taken unless strong=True.  Returns (rho, ux, uy, p,
+    beta)."""
+    speed = float(np.hypot(ux1, uy1))
+    M = speed / sound_speed(rho1, p1, gamma)
+    th = abs(turn)
+    g = lambda b: 2.0 / np.tan(b) * (M * M * np.sin(b) ** 2 - 1.0) / (
+        M * M * (gamma + np.cos(2.0 * b)) + 2.0) - np.tan(th)
+    mu = np.arcsin(1.0 / M)
+    bs = np.linspace(mu + 1e-9, np.pi / 2 - 1e-9, 20001)
+    gv = np.array([g(b) for b in bs])
+    k = int(np.argmax(gv))
+    if gv[k] < 0:
+        raise ValueError("turn angle beyond the maximum for this Mach number (detached shock)")
+    beta = brentq(g, bs[k], bs[-1]) if strong else brentq(g, bs[0], bs[k])
+    # unit normal pointing downstream: the shock line makes angle beta with
+    # the flow, on the side the flow turns towards
+    phi = np.arctan2(uy1, ux1)
+    sgn = 1.0 if turn >= 0 else -1.0
+    line = phi + sgn * beta
+    n = np.array([np.sin(line), -np.cos(line)]) * sgn
+    if n[0] * ux1 + n[1] * uy1 < 0:
+        n = -n
+    rho2, ux2, uy2, p2 = oblique_shock(rho1, ux1, uy1, p1, n, gamma)
+    return rho2, ux2, uy2, p2, beta

@@ -79,10 +79,10 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const S* __restrict__ f, c
                                                       S* __restrict__ abar, const Model<S> M,
                                                       const Grid<S> G, long long level,
                                                       double* __restrict__ taup) {
-    __shared__ double sh[kThreads];
+    __shared__ double sh[kThreads / 32];
     const long long n = (long long)G.nx * G.ny;
     const long long q = blockIdx.x * (long long)kThreads + threadIdx.x;
-    double tsum = 0.0;
+    S tsum = S(0);
     if (q < n) {
         const int iy = (int)(q / G.nx), ix = (int)(q % G.nx);
         const size_t pl = (size_t)G.plane;
@@ -102,7 +102,7 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const S* __restrict__ f, c
         S tn = S(0);
 #pragma unroll
         for (int i = 0; i < 9; ++i) tn += av[i] * (fe[i] - fv[i]);
-        tsum = (double)tn;
+        tsum = tn;
         S h[4], g[9];
         feq_vjp(M, rho, ux, uy, T, av, h);
         moments_vjp(M, rho, ux, uy, T, h, g);
@@ -136,13 +136,17 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const S* __restrict__ f, c
             abar[j * pl + c] = o;
         }
     }
-    sh[threadIdx.x] = tsum;
+    // warp sums in the storage precision (fixed shuffle tree), then the
+    // block's eight warp sums in FP64 in a fixed order
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) tsum += __shfl_down_sync(0xffffffffu, tsum, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x / 32] = (double)tsum;
     __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
-        __syncthreads();
+    if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kThreads / 32; ++w) t += sh[w];
+        taup[blockIdx.x] += t;
     }
-    if (threadIdx.x == 0) taup[blockIdx.x] += sh[0];
 }
 
 // Seed: abar_j = sum_m qbar_m dq_m/df_j at the level f (qbar may have null

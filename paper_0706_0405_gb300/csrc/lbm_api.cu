@@ -199,6 +199,12 @@ Grid<S> build_grid(const lbm_ctx& c, const Model<double>& M) {
         G.kind_hi[s] = c.bc[s].kind_hi;
         G.split0[s] = c.bc[s].split0;
         G.split_speed[s] = c.bc[s].split_speed;
+        G.split_moving[s] = c.bc[s].split_speed != 0.0 ? 1 : 0;
+        // first along-index whose cell centre is not below the fixed split
+        const int len = (s == LBM_SIDE_LEFT || s == LBM_SIDE_RIGHT) ? c.ny : c.nx;
+        int idx = 0;
+        while (idx < len && ((double)idx + 0.5) * c.dx < c.bc[s].split0) ++idx;
+        G.split_index[s] = idx;
         double lo[9], hi[9];
         const double* a = c.bc[s].state_lo;
         const double* b = c.bc[s].state_hi;

@@ -51,6 +51,8 @@ struct Grid {
     int nx, ny, pitch;
     long long plane;              // elements per population plane = (ny + 2) * pitch
     int kind_lo[4], kind_hi[4];
+    int split_moving[4];          // 1 if split_speed != 0
+    int split_index[4];           // fixed splits: first along-index in the "hi" part
     double split0[4], split_speed[4];
     double dt, dx;
     S feq[4][2][9];               // f^eq of each side's lo / hi Dirichlet state
@@ -73,7 +75,9 @@ __device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-__device__ __forceinline__ float rcp_(float a) { return __frcp_rn(a); }
+// FP32: the hardware approximate reciprocal (about 1 ulp); the error of the
+// FP32 modes is set by the FP32 storage of f, far above that.
+__device__ __forceinline__ float rcp_(float a) { return __fdividef(1.0f, a); }
 __device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
@@ -134,9 +138,12 @@ __device__ __forceinline__ void moments(const S (&f)[9], const Model<S>& M, S& r
     }
 }
 
-// Equilibrium of Eqs. (e16)-(e18): f_i^eq = rho (A_i + B_i v.u + D_i (v.u)^2).
+// Equilibrium of Eqs. (e16)-(e18) times a factor:
+// fe_i = scale (A_i + B_i v.u + D_i (v.u)^2); scale = rho gives f^eq, scale =
+// omega rho gives the relaxation term omega f^eq of the update directly.
 template <typename S>
-__device__ __forceinline__ void equilibrium(const Model<S>& M, S rho, S ux, S uy, S T, S (&fe)[9]) {
+__device__ __forceinline__ void equilibrium_scaled(const Model<S>& M, S scale, S ux, S uy, S T, S (&fe)[9]) {
+    const S rho = scale;
     const S u2 = fma_(ux, ux, mul_(uy, uy));
     const S A1 = fma_(M.a1u, u2, fma_(M.a1T, T, M.a1c));
     const S A5 = fma_(M.a5u, u2, fma_(M.a5T, T, M.a5c));
@@ -145,24 +152,36 @@ __device__ __forceinline__ void equilibrium(const Model<S>& M, S rho, S ux, S uy
     const S p = mul_(M.c1, ux), q = mul_(M.c1, uy);               // v.u of i = 3, 4 (-: 1, 2)
     const S r = mul_(M.d, add_(ux, uy)), m = mul_(M.d, sub_(ux, uy));  // v.u of i = 7, 6 (-: 5, 8)
     fe[0] = mul_(rho, mul_(M.k0, T));
-    const S sp = fma_(mul_(M.D1, p), p, A1), sq = fma_(mul_(M.D1, q), q, A1);
-    const S sr = fma_(mul_(M.D5, r), r, A5), sm = fma_(mul_(M.D5, m), m, A5);
-    fe[1] = mul_(rho, fma_(-B1, p, sp));
-    fe[3] = mul_(rho, fma_(B1, p, sp));
-    fe[2] = mul_(rho, fma_(-B1, q, sq));
-    fe[4] = mul_(rho, fma_(B1, q, sq));
-    fe[5] = mul_(rho, fma_(-B5, r, sr));
-    fe[7] = mul_(rho, fma_(B5, r, sr));
-    fe[6] = mul_(rho, fma_(B5, m, sm));
-    fe[8] = mul_(rho, fma_(-B5, m, sm));
+    // rho (A + D (v.u)^2) and rho B per group, then fe = rho (A + D (v.u)^2) +- rho B v.u
+    const S sp = mul_(rho, fma_(mul_(M.D1, p), p, A1)), sq = mul_(rho, fma_(mul_(M.D1, q), q, A1));
+    const S sr = mul_(rho, fma_(mul_(M.D5, r), r, A5)), sm = mul_(rho, fma_(mul_(M.D5, m), m, A5));
+    const S rB1 = mul_(rho, B1), rB5 = mul_(rho, B5);
+    fe[1] = fma_(-rB1, p, sp);
+    fe[3] = fma_(rB1, p, sp);
+    fe[2] = fma_(-rB1, q, sq);
+    fe[4] = fma_(rB1, q, sq);
+    fe[5] = fma_(-rB5, r, sr);
+    fe[7] = fma_(rB5, r, sr);
+    fe[6] = fma_(rB5, m, sm);
+    fe[8] = fma_(-rB5, m, sm);
 }
 
-// Update of one population from its five-point star and its equilibrium
+template <typename S>
+__device__ __forceinline__ void equilibrium(const Model<S>& M, S rho, S ux, S uy, S T, S (&fe)[9]) {
+    equilibrium_scaled(M, rho, ux, uy, T, fe);
+}
+
+// omega f^eq (the relaxation term of Eq. SEC-VON-11 with omega = dt / tau).
+template <typename S>
+__device__ __forceinline__ void omega_equilibrium(const Model<S>& M, S rho, S ux, S uy, S T, S (&ofe)[9]) {
+    equilibrium_scaled(M, mul_(M.omega, rho), ux, uy, T, ofe);
+}
+
+// Update of one population from its five-point star and omega f^eq
 // (Eq. SEC-VON-11 with the folded weights of Model::w).
 template <typename S>
-__device__ __forceinline__ S update(const Model<S>& M, int i, S fe, S c, S e, S w, S n, S s) {
-    S acc = mul_(M.omega, fe);
-    acc = fma_(M.w[i][0], c, acc);
+__device__ __forceinline__ S update(const Model<S>& M, int i, S ofe, S c, S e, S w, S n, S s) {
+    S acc = fma_(M.w[i][0], c, ofe);
     acc = fma_(M.w[i][1], e, acc);
     acc = fma_(M.w[i][2], w, acc);
     acc = fma_(M.w[i][3], n, acc);
@@ -174,9 +193,13 @@ __device__ __forceinline__ S update(const Model<S>& M, int i, S fe, S c, S e, S 
 // `along` for time level `level`: lo iff along < split0 + split_speed t with
 // t = level * dt, all in FP64 with explicit rounding so that the decision is
 // the same as a plain IEEE evaluation of that expression on any host.
+// Unsplit sides and sides with a fixed split carry the first "hi" index,
+// computed on the host with the same FP64 expression; only moving splits
+// (split_speed != 0) evaluate it here.
 template <typename S>
 __device__ __forceinline__ int side_part(const Grid<S>& G, int side, int along_index,
                                          long long level) {
+    if (!G.split_moving[side]) return along_index < G.split_index[side] ? 0 : 1;
     const double t = __dmul_rn((double)level, G.dt);
     const double split = __dadd_rn(G.split0[side], __dmul_rn(G.split_speed[side], t));
     const double along = __dmul_rn((double)along_index + 0.5, G.dx);
@@ -246,9 +269,10 @@ constexpr unsigned ST_TIMEOUT = 2u;      // a bounded device wait gave up
 constexpr unsigned ST_T_NONPOS = 4u;     // T <= 0 at some node (transient, allowed)
 
 // Health bits of one node's moments.
+// (A non-finite velocity makes T non-finite too, since T is formed from it.)
 template <typename S>
 __device__ __forceinline__ unsigned health(S rho, S ux, S uy, S T) {
-    if (!(rho > S(0)) || !isfinite(T) || !isfinite(ux + uy)) return ST_NONPHYSICAL;
+    if (!(rho > S(0)) || !isfinite(T)) return ST_NONPHYSICAL;
     return T > S(0) ? 0u : ST_T_NONPOS;
 }
 
@@ -258,6 +282,42 @@ __device__ __forceinline__ void report(unsigned* status, unsigned bits) {
     const unsigned m = __activemask();
     const unsigned any = __reduce_or_sync(m, bits);
     if (any && (threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicOr(status, any);
+}
+
+// ------------------------------------------------------ one node per thread
+// Reads the node and its four star neighbours of all nine planes (kCoherent:
+// through L2 only, for data written earlier in the same kernel by other
+// CTAs), updates it, writes nine values and, at an edge, the next level's
+// ghost cells.  Returns the node's health bits.
+template <typename S, bool kCoherent>
+__device__ __forceinline__ S load_s(const S* p) {
+    return kCoherent ? __ldcg(p) : __ldg(p);
+}
+
+template <typename S, int TM, bool kCoherent>
+__device__ __forceinline__ unsigned node_step(const S* __restrict__ fin, S* __restrict__ fout, const Model<S>& M,
+                                              const Grid<S>& G, int ix, int iy, long long level) {
+    const size_t pl = (size_t)G.plane;
+    const size_t c = cell(G, ix, iy);
+    S f[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) f[i] = load_s<S, kCoherent>(fin + i * pl + c);
+    S rho, ux, uy, T;
+    moments<S, TM>(f, M, rho, ux, uy, T);
+    const unsigned bits = health(rho, ux, uy, T);
+    S ofe[9];
+    omega_equilibrium(M, rho, ux, uy, T, ofe);
+    S o[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        const S* p = fin + i * pl + c;
+        o[i] = update(M, i, ofe[i], f[i], load_s<S, kCoherent>(p + 1), load_s<S, kCoherent>(p - 1),
+                      load_s<S, kCoherent>(p + G.pitch), load_s<S, kCoherent>(p - G.pitch));
+    }
+#pragma unroll
+    for (int i = 0; i < 9; ++i) fout[i * pl + c] = o[i];
+    if (ix == 0 || iy == 0 || ix == G.nx - 1 || iy == G.ny - 1) write_ghosts(G, fout, ix, iy, o, level + 1);
+    return bits;
 }
 
 // ------------------------------------------------- vectorised node group
@@ -339,10 +399,10 @@ __device__ __forceinline__ unsigned vec_group(const float* __restrict__ fin, flo
         float rho, ux, uy, T;
         moments<float, TM>(f, M, rho, ux, uy, T);
         if (k < nvalid) bits |= health(rho, ux, uy, T);
-        float fe[9];
-        equilibrium(M, rho, ux, uy, T, fe);
+        float ofe[9];
+        omega_equilibrium(M, rho, ux, uy, T, ofe);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) acc[i][k] = mul_(M.omega, fe[i]);
+        for (int i = 0; i < 9; ++i) acc[i][k] = ofe[i];
     }
 
     float* out = fout + c0;
@@ -360,11 +420,7 @@ __device__ __forceinline__ unsigned vec_group(const float* __restrict__ fin, flo
         float o[V];
 #pragma unroll
         for (int k = 0; k < V; ++k) {
-            float a = fma_(M.w[i][0], row[k + 1], acc[i][k]);
-            a = fma_(M.w[i][1], row[k + 2], a);
-            a = fma_(M.w[i][2], row[k], a);
-            a = fma_(M.w[i][3], Nn[k], a);
-            o[k] = fma_(M.w[i][4], Ss[k], a);
+            o[k] = update(M, i, acc[i][k], row[k + 1], row[k + 2], row[k], Nn[k], Ss[k]);
         }
         if (nvalid == V) {
             store_vec<V>(out + i * pl, o);

@@ -24,27 +24,7 @@ __global__ void __launch_bounds__(256) k_step_simple(const S* __restrict__ fin, 
     const int ix = blockIdx.x * blockDim.x + threadIdx.x;
     const int iy = blockIdx.y * blockDim.y + threadIdx.y;
     if (ix >= G.nx || iy >= G.ny) return;
-    const size_t pl = (size_t)G.plane;
-    const size_t c = cell(G, ix, iy);
-    S f[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) f[i] = __ldg(fin + i * pl + c);
-    S rho, ux, uy, T;
-    moments<S, TM>(f, M, rho, ux, uy, T);
-    report(status, health(rho, ux, uy, T));
-    S fe[9];
-    equilibrium(M, rho, ux, uy, T, fe);
-    S o[9];
-#pragma unroll
-    for (int i = 0; i < 9; ++i) {
-        const S* p = fin + i * pl + c;
-        o[i] = update(M, i, fe[i], f[i], __ldg(p + 1), __ldg(p - 1), __ldg(p + G.pitch),
-                      __ldg(p - G.pitch));
-    }
-#pragma unroll
-    for (int i = 0; i < 9; ++i) fout[i * pl + c] = o[i];
-    if (ix == 0 || iy == 0 || ix == G.nx - 1 || iy == G.ny - 1)
-        write_ghosts(G, fout, ix, iy, o, level + 1);
+    report(status, node_step<S, TM, false>(fin, fout, M, G, ix, iy, level));
 }
 
 // ------------------------------------------------- FP32 vectorised kernel
@@ -77,22 +57,25 @@ cudaError_t launch_vec(const float* fin, float* fout, const Model<float>& M, con
 }
 
 // ------------------------------------------------------ FP32 TMA tile kernel
-// Persistent CTAs of 64 x 8 threads walk 64 x 8-node tiles.  For each tile
+// Persistent CTAs of 32 x 8 threads walk 64 x 8-node tiles.  For each tile
 // one thread issues a single tiled tensor copy of the 72 x 10 x 9 box (4
 // extra columns on each side for 16-byte alignment, one extra row above and
 // below, all nine planes) into one of two shared-memory stages; the next
 // tile's box is in flight while the current one is computed.  Each thread
-// then reads its node's five-point star from shared memory (no global loads,
-// no 64-bit address arithmetic), and writes its nine values.  Waits are
-// bounded: on give-up the CTA raises ST_TIMEOUT, drains, returns.
+// updates two x-adjacent nodes: it reads their values and those of the rows
+// above and below as 8-byte pairs from shared memory, the outer x neighbours
+// as single floats, and writes 8-byte pairs (no global loads, no per-load
+// 64-bit address arithmetic).  Waits are bounded: on give-up the CTA raises
+// ST_TIMEOUT, drains its copies in flight and returns.
 constexpr int kTileX = 64, kTileY = 8;
+constexpr int kTileThreads = (kTileX / 2) * kTileY;
 constexpr int kBoxX = kTileX + 8, kBoxY = kTileY + 2;
 constexpr int kBoxFloats = kBoxX * kBoxY * 9;
 constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages start on 128-byte boundaries
 constexpr size_t kTileSmem = 128 + sizeof(float) * 2 * kStageFloats + 2 * sizeof(uint64_t);
 
 template <int TM>
-__global__ void __launch_bounds__(kTileX * kTileY, 2)
+__global__ void __launch_bounds__(kTileThreads, 3)
     k_step_tile(const __grid_constant__ CUtensorMap tmap, float* __restrict__ fout, const Model<float> M,
                 const Grid<float> G, long long level, unsigned* status, int tiles_x, int ntiles) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -101,7 +84,7 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2)
     float* box = reinterpret_cast<float*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(float) * 2 * kStageFloats);
     __shared__ int abort_flag;
-    const int tid = threadIdx.x, tx = tid % kTileX, ty = tid / kTileX;
+    const int tid = threadIdx.x, tx = tid % (kTileX / 2), ty = tid / (kTileX / 2);
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -122,6 +105,7 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2)
         issued = 0;
     }
     const size_t pl = (size_t)G.plane;
+    constexpr int P = kBoxX * kBoxY;  // floats per plane in the box
     unsigned bits = 0;
     for (int k = 0;; ++k) {
         const int t = blockIdx.x + k * gridDim.x;
@@ -141,25 +125,56 @@ __global__ void __launch_bounds__(kTileX * kTileY, 2)
             continue;
         }
         waited = k;
-        const int ix = (t % tiles_x) * kTileX + tx, iy = (t / tiles_x) * kTileY + ty;
-        if (ix >= G.nx || iy >= G.ny) continue;
-        const float* b = box + (k & 1) * kStageFloats + (ty + 1) * kBoxX + (tx + 4);
-        constexpr int P = kBoxX * kBoxY;  // floats per plane in the box
-        float f[9];
+        const int ix0 = (t % tiles_x) * kTileX + 2 * tx, iy = (t / tiles_x) * kTileY + ty;
+        if (ix0 >= G.nx || iy >= G.ny) continue;
+        const int nvalid = min(2, G.nx - ix0);
+        // centre of node ix0 in the box: row ty + 1, column 2 tx + 4 (8-byte aligned)
+        const float* b = box + (k & 1) * kStageFloats + (ty + 1) * kBoxX + (2 * tx + 4);
+        float2 C[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) f[i] = b[i * P];
-        float rho, ux, uy, T;
-        moments<float, TM>(f, M, rho, ux, uy, T);
-        bits |= health(rho, ux, uy, T);
-        float fe[9], o[9];
-        equilibrium(M, rho, ux, uy, T, fe);
+        for (int i = 0; i < 9; ++i) C[i] = *reinterpret_cast<const float2*>(b + i * P);
+        float acc[9][2];
 #pragma unroll
-        for (int i = 0; i < 9; ++i)
-            o[i] = update(M, i, fe[i], f[i], b[i * P + 1], b[i * P - 1], b[i * P + kBoxX], b[i * P - kBoxX]);
-        const size_t c = cell(G, ix, iy);
+        for (int j = 0; j < 2; ++j) {
+            float f[9];
 #pragma unroll
-        for (int i = 0; i < 9; ++i) fout[i * pl + c] = o[i];
-        if (ix == 0 || iy == 0 || ix == G.nx - 1 || iy == G.ny - 1) write_ghosts(G, fout, ix, iy, o, level + 1);
+            for (int i = 0; i < 9; ++i) f[i] = j ? C[i].y : C[i].x;
+            float rho, ux, uy, T;
+            moments<float, TM>(f, M, rho, ux, uy, T);
+            if (j < nvalid) bits |= health(rho, ux, uy, T);
+            float ofe[9];
+            omega_equilibrium(M, rho, ux, uy, T, ofe);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) acc[i][j] = ofe[i];
+        }
+        const size_t c0 = cell(G, ix0, iy);  // 8-byte aligned: ix0 + PADX is even
+        float* out = fout + c0;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float* bp = b + i * P;
+            const float2 Nn = *reinterpret_cast<const float2*>(bp + kBoxX);
+            const float2 Ss = *reinterpret_cast<const float2*>(bp - kBoxX);
+            const float Wv = bp[-1], Ev = bp[2];
+            float2 o;
+            o.x = update(M, i, acc[i][0], C[i].x, C[i].y, Wv, Nn.x, Ss.x);
+            o.y = update(M, i, acc[i][1], C[i].y, Ev, C[i].x, Nn.y, Ss.y);
+            if (nvalid == 2)
+                *reinterpret_cast<float2*>(out + i * pl) = o;
+            else
+                out[i * pl] = o.x;
+        }
+        // edge nodes also write the next level's ghost cells (values read back)
+        const bool edge_row = iy == 0 || iy == G.ny - 1;
+        if (edge_row || ix0 == 0 || ix0 + nvalid == G.nx) {
+            for (int j = 0; j < nvalid; ++j) {
+                const int ix = ix0 + j;
+                if (!(edge_row || ix == 0 || ix == G.nx - 1)) continue;
+                float v[9];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) v[i] = out[i * pl + j];
+                write_ghosts(G, fout, ix, iy, v, level + 1);
+            }
+        }
     }
     __syncthreads();
     if (abort_flag) {  // a wait of the last tile gave up
@@ -191,13 +206,13 @@ cudaError_t launch_tile(const CUtensorMap& tmap, float* fout, const Model<float>
             int dev = 0, sms = 0, per_sm = 0;
             cudaGetDevice(&dev);
             cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileX * kTileY, smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem);
             full_wave = sms * (per_sm > 0 ? per_sm : 1);
         }
         grid = full_wave;
     }
     if (grid > ntiles) grid = ntiles;
-    kern<<<grid, kTileX * kTileY, smem, st>>>(tmap, fout, M, G, level, status, tiles_x, ntiles);
+    kern<<<grid, kTileThreads, smem, st>>>(tmap, fout, M, G, level, status, tiles_x, ntiles);
     return cudaGetLastError();
 }
 
@@ -314,7 +329,7 @@ __global__ void __launch_bounds__(TX, 2)
                 moments<float, TM>(f, M, rho, ux, uy, T);
                 report(status, health(rho, ux, uy, T));
                 float fe[9];
-                equilibrium(M, rho, ux, uy, T, fe);
+                omega_equilibrium(M, rho, ux, uy, T, fe);
 #pragma unroll
                 for (int i = 0; i < 9; ++i)
                     o[i] = update(M, i, fe[i], C[i], sc[i * WPAD + tid + 5], sc[i * WPAD + tid + 3],

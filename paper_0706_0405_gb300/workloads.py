@@ -204,6 +204,30 @@ def dmr(ny: int = 1024, alpha: float = 0.1, lam_scale: float = 2.0, t_end: float
                     "slope": 1.0 / s3})
 
 
+def regular_reflection(ny: int = 300, alpha: float = 0.1, lam_scale: float = 2.0,
+                       t_end: float = 2.5, steps: int | None = None) -> Problem:
+    """Steady regular reflection of a 30-degree shock (Sec. 4.2, Fig. 11,
+    Eq. Riemann-3): domain 9 x 3 on a 3 ny x ny grid (900 x 300, dx = 0.01 by
+    default), Mach-10 inflow (rho, u, v, p) = (1, 10, 0, 1/1.4) on the left
+    and as the initial state everywhere, the post-shock state
+    (5, 8, -2 sqrt(3), 29/1.4) (printed as (5.0, 8.0, -3.4641, 20.7143)) on
+    the top, a reflecting wall at the bottom and zero-gradient outflow on the
+    right; c1 = 10, c2 = 20, eta0 = 15 (Fig. 11).  The paper's dt = 1.5e-4 is
+    alpha = 0.3, which grows at the inflow state by the von Neumann matrix;
+    alpha = 0.1 with lambda = 2 x Eq. 13 is neutral at all three states of the
+    exact solution."""
+    nx, dx = 3 * ny, 3.0 / ny
+    c1, c2, eta0 = 10.0, 20.0, 15.0
+    dt = alpha * dx / c2
+    inflow = _ptoT((1.0, 10.0, 0.0, 1.0 / 1.4))
+    top = _ptoT((5.0, 8.0, -2.0 * math.sqrt(3.0), 29.0 / 1.4))
+    sides = (Side("dirichlet", state_lo=inflow, state_hi=inflow), Side("outflow"), Side("reflect"),
+             Side("dirichlet", state_lo=top, state_hi=top))
+    n = int(round(t_end / dt)) if steps is None else steps
+    return Problem(f"regref_{nx}x{ny}", nx, ny, B_AIR, dt, dt, dx, c1, c2, eta0, 0.25,
+                   lambda_eq13(c1, dx, lam_scale), sides, n, {"kind": "uniform", "state": inflow})
+
+
 def uniform(nx, ny, state, c1=3.0, c2=9.0, eta0=5.0, dx=0.01, alpha=0.05, tau=None,
             beta=0.25, lam_scale=1.0, sides=None, b=B_AIR, steps=100) -> Problem:
     """A uniform state (rho, ux, uy, T) (for invariance tests)."""

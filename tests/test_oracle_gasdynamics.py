@@ -151,3 +151,37 @@ def test_oracle_steady_mach3_shock_stays_put():
     assert down[0][0, -20] == pytest.approx(rho2, rel=0.01)
     assert down[1][0, -20] == pytest.approx(u2, rel=0.01)
     assert down[0][0, -20] * down[3][0, -20] == pytest.approx(p2, rel=0.01)
+
+
+def test_oblique_shock_for_turn_inverts_the_incident_shock(paper_values):
+    """Turning the Mach-10 inflow by the deflection of the Eq. (Riemann-3) top
+    state gives back the 30-degree shock; the reflected shock that turns that
+    state back along the wall has the textbook weak-solution angle and leaves
+    the flow parallel to the wall."""
+    r, u1, u2, p = paper_values["riemann3_inflow_rho_u1_u2_p"]
+    top = gd.oblique_shock(r, u1, u2, p, (0.5, math.sqrt(3) / 2), G)
+    turn = math.atan2(top[2], top[1])
+    inc = gd.oblique_shock_for_turn(r, u1, u2, p, turn, G)
+    assert math.degrees(inc[4]) == pytest.approx(paper_values["regular_reflection_angle_deg"][0], abs=1e-9)
+    assert inc[:4] == pytest.approx(top, rel=1e-10)
+    ref = gd.oblique_shock_for_turn(*top, -turn, G)
+    assert abs(ref[2]) < 1e-12 * abs(ref[1])
+    # mass flux through the reflected shock is continuous; the shock line
+    # leans by beta from the oncoming flow towards the side the flow turns to
+    line = math.atan2(top[2], top[1]) + ref[4]
+    n = (math.sin(line), -math.cos(line))
+    m_in = top[0] * (top[1] * n[0] + top[2] * n[1])
+    m_out = ref[0] * (ref[1] * n[0] + ref[2] * n[1])
+    assert abs(m_in - m_out) < 1e-9 * abs(m_in)
+
+
+def test_regular_reflection_states_are_vetted():
+    from oracle import vonneumann as vn
+    p = W.regular_reflection()
+    top = p.sides[3].state_lo
+    r, u, v, T = top
+    ref = gd.oblique_shock_for_turn(r, u, v, r * T, -math.atan2(v, u), G)
+    states = [p.setup["state"], top, (ref[0], ref[1], ref[2], ref[3] / ref[0])]
+    for st in states:
+        g = vn.max_growth(st, p.b, p.c1, p.c2, p.eta0, p.dt, p.dx, p.tau, p.beta, np.array(p.lam))
+        assert g <= 1.0 + 1e-9, (st, g)
