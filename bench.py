@@ -121,9 +121,10 @@ def hbm_peak():
 
 def recorded_traffic(kernel: str):
     """DRAM bytes per launch from profiles/dram_traffic.txt if that capture was
-    taken on the current library sources (same source hash), else None."""
+    taken on the kernel's current sources (same hash of the files that define
+    it), else None."""
     from paper_0706_0405_gb300 import build as B
-    src = B.source_hash()
+    src = B.kernel_hash(kernel)
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as fh:
             for line in fh:
@@ -235,7 +236,7 @@ def run_ours(args, world, dist):
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                      "frac": round(achieved / peak, 4), "traffic": recorded_traffic(kname),
                      "peak_kind": peak_kind, "algorithmic_bytes_per_node": bpn,
-                     "kernel": kname, "kernel_ms": round(kernel_ms, 5), "src": B.source_hash()},
+                     "kernel": kname, "kernel_ms": round(kernel_ms, 5), "src": B.kernel_hash(kname)},
         "clocks": clocks.summary(),
         "gpu_launches": args.steps,
     }
@@ -267,6 +268,7 @@ def run_ours(args, world, dist):
 
 
 def extras(args, p, fields, stream):
+    import numpy as np
     import torch
     from paper_0706_0405_gb300 import lbm
     from paper_0706_0405_gb300 import workloads as W
@@ -352,6 +354,29 @@ def extras(args, p, fields, stream):
                     "cuda_graph": bool(graph),
                     "working_set_MB": round(sum(2 * 9 * (b.ny + 2) * ((b.nx + 8 + 31) // 32 * 32) * 4
                                                 for b in probs) / 1e6, 1)}
+
+    # von Neumann scan: 9 x 9 complex amplification matrices per second
+    # (every tube's constants at 16 states, 4 directions, 31 wave numbers)
+    rng = np.random.default_rng(0)
+    cases = []
+    for b in probs:
+        for _ in range(16):
+            cases.append(lbm.vn_case(b, (rng.uniform(0.5, 10), rng.uniform(-1, 1) * b.c1, 0.0,
+                                         rng.uniform(0.5, 5))))
+    nk, dirs = 31, lbm.DIRECTIONS
+    radius = torch.empty((len(cases), len(dirs), nk), dtype=torch.float64, device="cuda")
+    lbm.lbm_vn_scan(cases, dirs, nk, radius, None, stream.cuda_stream)
+    torch.cuda.synchronize()
+    s.record(stream)
+    reps = 5
+    for _ in range(reps):
+        lbm.lbm_vn_scan(cases, dirs, nk, radius, None, stream.cuda_stream)
+    e.record(stream)
+    e.synchronize()
+    vsecs = s.elapsed_time(e) / 1e3 / reps
+    out["vn_scan"] = {"matrices": len(cases) * len(dirs) * nk, "ms": round(vsecs * 1e3, 3),
+                      "matrices_per_s": round(len(cases) * len(dirs) * nk / vsecs, 0),
+                      "note": "per call, host case set-up and scratch allocation included"}
     return out
 
 

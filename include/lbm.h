@@ -335,6 +335,54 @@ lbm_ctx* lbm_batch_problem(lbm_batch* batch, int p);
  * capture failed and the launch runs directly). */
 lbm_status lbm_batch_info(const lbm_batch* batch, int* grid, int* ntiles, int* graph);
 
+/* -------------------------------------------------- von Neumann scanner
+ * Linear stability of the scheme about a uniform state (Sec. 3): a Fourier
+ * mode exp(i k.x) of a perturbation of f is multiplied each step by the 9 x 9
+ * amplification matrix of Eqs. (SEC-VON-8, SEC-VON-12),
+ *   G(k) = diag(W_i(k)) + (dt / tau) d f^eq / d f,
+ * with W_i(k) the symbol of the step's five-point stencil for velocity i
+ * (beta-upwind advection of Eqs. SEC-VON-2a/2b, the lambda_i Laplacian and
+ * the -dt/tau of the relaxation) and d f^eq / d f the Jacobian of the
+ * equilibrium of the moments at the state (Eqs. e4, e5, e7, e16-e18).  The
+ * scheme damps every mode when the spectral radius max|eig G| <= 1 (Figs.
+ * 2-7 plot it against k dx).
+ *
+ * One case: the constants a context would get from lbm_create and the
+ * uniform state (rho, ux, uy, T). */
+typedef struct lbm_vn_case {
+    double b, tau, dt, dx;
+    lbm_dvm dvm;
+    lbm_dissipation diss;
+    double state[4];
+} lbm_vn_case;
+
+/* For every case c, direction d and m = 0 .. nk - 1, the spectral radius of
+ * G(k) at k dx = (pi m / (nk - 1)) (dirs[2d], dirs[2d + 1]) (k = 0 when
+ * nk = 1; the paper scans k dx from 0 to pi in 31 points along x):
+ *   radius[(c * ndirs + d) * nk + m]      (ncases x ndirs x nk doubles)
+ *   growth[c] = max over d and m          (ncases doubles)
+ * The eigenvalues come from a Hessenberg reduction and the shifted QR
+ * iteration in FP64, one matrix per GPU thread; an entry is NaN if the
+ * iteration did not converge in 60 sweeps per eigenvalue (growth is then NaN).
+ *  - cases (ncases) and dirs (2 x ndirs ints, each pair in [-1024, 1024] and
+ *    not (0, 0), e.g. (1,0), (0,1), (1,1), (1,-1)) are host memory, read
+ *    before the call returns.
+ *  - radius and growth may each be NULL (not both), device memory (written
+ *    asynchronously on `stream`) or host memory (the call then synchronises
+ *    `stream`).  The caller owns them.
+ *  - stream: a cudaStream_t (NULL = the legacy default stream).  The call
+ *    allocates its scratch (81 doubles per case, plus radius when that is not
+ *    in device memory) with cudaMallocAsync on that stream and frees it in
+ *    stream order.
+ *  - ncases = 0 does nothing.  LBM_E_INVAL: ncases < 0, NULL cases / dirs,
+ *    ndirs outside [1, 64], nk outside [1, 65536], ncases * ndirs * nk
+ *    >= 2^31, or a case with b, tau, dt, dx, c1, c2, eta0 not finite and > 0,
+ *    c1 == c2, beta outside [0, 1/2], a negative lambda, rho or T not > 0
+ *    (the message, from lbm_last_error(NULL), names the case).  LBM_E_NOMEM /
+ *    LBM_E_CUDA if the scratch or a launch fails. */
+lbm_status lbm_vn_scan(const lbm_vn_case* cases, int ncases, const int* dirs, int ndirs, int nk,
+                       double* radius, double* growth, void* stream);
+
 /* FP64 and FP32 FMA throughput (TFLOP/s, 2 flops per FMA) of the current
  * device, from chains of dependent FMAs on every SM (~0.1 s).  Not from the
  * paper: the benchmark's ceiling for the FP64 step, which is bounded by the

@@ -43,15 +43,34 @@ def _deps():
         os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
 
 
-def source_hash() -> str:
-    """Short hash of every source the library is built from (used to tell
-    whether a recorded profile still describes the current kernels)."""
+# Sources that define each profiled kernel's code: the kernel's own file and
+# every header with device code it calls.
+KERNEL_SOURCES = {
+    "k_step_tile": ("lbm_step.cu", "lbm_device.cuh", "lbm_ptx.cuh"),
+    "k_step_vec": ("lbm_step.cu", "lbm_device.cuh", "lbm_ptx.cuh"),
+    "k_step_simple": ("lbm_step.cu", "lbm_device.cuh", "lbm_ptx.cuh"),
+    "k_step_ring": ("lbm_step.cu", "lbm_device.cuh", "lbm_ptx.cuh"),
+}
+
+
+def source_hash(names=None) -> str:
+    """Short hash of the sources the library is built from, or of the files
+    with the given base names (used to tell whether a recorded profile still
+    describes the current kernels)."""
     h = hashlib.sha1()
     for path in sorted(_deps()):
+        if names is not None and os.path.basename(path) not in names:
+            continue
         with open(path, "rb") as fh:
             h.update(os.path.basename(path).encode())
             h.update(fh.read())
     return h.hexdigest()[:12]
+
+
+def kernel_hash(kernel: str) -> str:
+    """source_hash of the files that define ``kernel`` (all sources if the
+    kernel is not listed)."""
+    return source_hash(KERNEL_SOURCES.get(kernel))
 
 
 def stale() -> bool:

@@ -84,4 +84,15 @@ cudaError_t launch_batch(const BatchProb* probs, const int4* tiles, int ntiles, 
 template <int TM>
 int batch_max_grid();
 
+// von Neumann scan (lbm_vonneumann.cu): one case is the step's constants
+// (folded weights, omega, equilibrium coefficients) and a uniform state.
+struct VnCase {
+    Model<double> M;
+    double rho, ux, uy, T;
+};
+// J: scratch of 81 doubles per case; radius: ncases x ndirs x nk; growth
+// (may be null): ncases.  All device memory.
+cudaError_t launch_vn_scan(const VnCase* cases, int ncases, const int2* dirs, int ndirs, int nk, double* J,
+                           double* radius, double* growth, cudaStream_t st);
+
 }  // namespace lbm

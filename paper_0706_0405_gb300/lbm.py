@@ -31,7 +31,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init", "lbm_step"
            "lbm_record", "lbm_adjoint_seed", "lbm_adjoint_step", "lbm_feq_vjp",
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_init",
            "lbm_batch_step", "lbm_batch_sync", "lbm_batch_problem", "lbm_batch_info",
-           "lbm_probe_rates")
+           "lbm_probe_rates", "lbm_vn_scan")
 LBM_FLAG_NONPHYSICAL, LBM_FLAG_TIMEOUT, LBM_FLAG_T_NONPOSITIVE = 1, 2, 4
 
 
@@ -59,6 +59,12 @@ class lbm_problem(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("b", ctypes.c_double),
                 ("tau", ctypes.c_double), ("dt", ctypes.c_double), ("dx", ctypes.c_double),
                 ("dvm", lbm_dvm), ("diss", lbm_dissipation), ("bc", lbm_bc * 4)]
+
+
+class lbm_vn_case(ctypes.Structure):
+    _fields_ = [("b", ctypes.c_double), ("tau", ctypes.c_double), ("dt", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dvm", lbm_dvm), ("diss", lbm_dissipation),
+                ("state", ctypes.c_double * 4)]
 
 
 class lbm_launch(ctypes.Structure):
@@ -125,6 +131,8 @@ def load():
                                       ctypes.POINTER(lbm_dvm), ctypes.POINTER(ctypes.c_double), _VP],
                                      ctypes.c_int),
         "lbm_get_launch": ([ctx, ctypes.POINTER(lbm_launch)], ctypes.c_int),
+        "lbm_vn_scan": ([ctypes.POINTER(lbm_vn_case), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                         ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
         "lbm_autotune": ([ctx, ctypes.c_int, ctypes.POINTER(lbm_launch),
                           ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
     }
@@ -296,6 +304,49 @@ def lbm_probe_rates():
     if st != LBM_OK:
         raise LbmError(st, "lbm_probe_rates failed")
     return a.value, b.value
+
+
+DIRECTIONS = ((1, 0), (0, 1), (1, 1), (1, -1))
+
+
+def lbm_vn_scan(cases, dirs, nk, radius=None, growth=None, stream=None):
+    """Spectral radius of the amplification matrix for every case (a sequence
+    of lbm_vn_case), direction (pairs of ints) and nk wave numbers in
+    [0, pi] into radius (ncases x ndirs x nk doubles) and its maximum per case
+    into growth (ncases doubles); either may be None, a CUDA tensor or a host
+    array."""
+    cases = list(cases)
+    arr = (lbm_vn_case * max(1, len(cases)))(*cases)
+    flat = [int(v) for d in dirs for v in d]
+    darr = (ctypes.c_int * max(1, len(flat)))(*flat)
+    st = load().lbm_vn_scan(arr, len(cases), darr, len(flat) // 2, int(nk), _ptr(radius), _ptr(growth),
+                            _ptr(stream))
+    if st != LBM_OK:
+        raise LbmError(st, load().lbm_last_error(None).decode())
+
+
+def vn_case(p, state) -> lbm_vn_case:
+    """lbm_vn_case of a problem description (attributes of workloads.Problem)
+    linearised about the uniform state (rho, ux, uy, T)."""
+    q = lbm_vn_case()
+    q.b, q.tau, q.dt, q.dx = float(p.b), float(p.tau), float(p.dt), float(p.dx)
+    q.dvm = lbm_dvm(p.c1, p.c2, p.eta0)
+    q.diss.beta = float(p.beta)
+    for i in range(9):
+        q.diss.lambda_[i] = float(p.lam[i])
+    for k in range(4):
+        q.state[k] = float(state[k])
+    return q
+
+
+def vn_scan(cases, dirs=DIRECTIONS, nk: int = 31):
+    """(radius, growth) as CUDA tensors, radius shaped (ncases, ndirs, nk)."""
+    import torch
+    cases = list(cases)
+    radius = torch.empty((len(cases), len(dirs), nk), dtype=torch.float64, device="cuda")
+    growth = torch.empty((len(cases),), dtype=torch.float64, device="cuda")
+    lbm_vn_scan(cases, dirs, nk, radius, growth, torch.cuda.current_stream().cuda_stream)
+    return radius, growth
 
 
 def _bcheck(b, status):

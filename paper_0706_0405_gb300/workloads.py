@@ -130,6 +130,23 @@ def mach30_tube(nx: int = 1200, alpha: float = 0.05, c1: float = 33.0, c2: float
                    0.5 * nx * 0.01, c1, c2, eta0, alpha=alpha, steps=steps, lam_scale=lam_scale)
 
 
+def mach30_fig8(beta: float = 0.25, lam0_scale: float = 2.0, nx: int = 1600, t_end: float = 0.36,
+                steps: int | None = None) -> Problem:
+    """Eq. (Riemann-1) to t = 0.36 with dx = 0.01 (Figs. 8, 9): every wave
+    moves right (left shock at 12, contact at 15, right shock at 18), so the
+    tube is [0, 16] with the diaphragm at 6 and the fronts end near 10.3 and
+    12.5.  lambda_1..8 = 2 x Eq. 13; lambda_0 = lam0_scale c1 dx (Fig. 9b
+    sweeps it); beta = 0 gives the first-order upwind scheme of Fig. 9a.
+    DVM constants c1 = 33, c2 = 80, eta0 = 40, alpha = 0.05, tau = dt (the
+    paper's set is not stable by the von Neumann matrix, see mach30_tube)."""
+    c1, dx = 33.0, 16.0 / nx
+    p = riemann(f"mach30_fig8_{nx}x4", nx, 4, 16.0, (1.4, 30.0, 0.0, 1.0), (1.4, 0.0, 0.0, 1.0), 6.0,
+                c1, 80.0, 40.0, alpha=0.05, beta=beta, lam_scale=2.0,
+                t_end=t_end if steps is None else None, steps=steps or 0)
+    lam = (lam0_scale * c1 * dx,) + tuple(p.lam[1:])
+    return replace(p, lam=lam)
+
+
 def mach3_2048x256(steps: int = 1000) -> Problem:
     """Mach-3 tube for the adjoint: (rho, u, p)_L = (1.4, 3, 1), (rho, u, p)_R
     = (1.4, 0, 1) (sound speed 1, so Mach 3) on [0, 1] x [0, 0.125],
@@ -144,17 +161,30 @@ def batch_riemann(count: int = 256, seed: int = 0, steps: int = 1000, ny: int = 
     rows, diaphragm at 0.5; (rho, p)_L = (r, r) with r = exp(U[0, ln 1000]),
     (rho, p)_R = (1, 1) (T = 1 on both sides), left velocity M sqrt(1.4) with
     M ~ U[0, 30] (Mach M), right at rest.  DVM constants per tube:
-    c1 = max(3, 1.1 u_L + 2), c2 = 2.4 c1, eta0 = 1.2 c1, lambda = 2 x Eq. 13,
-    dt = 0.05 dx / c2, tau = dt (max|omega| = 1 at the left, right and star
-    states, checked by the tests)."""
+    c1 = max(3, 1.1 u_L + 2, 1.05 u* + 0.5), c2 = 2.4 c1, eta0 = 1.2 c1,
+    lambda = 2 x Eq. 13, dt = 0.05 dx / c2, tau = dt.  u* is the
+    two-rarefaction estimate of the star velocity (Toro, Riemann Solvers and
+    Numerical Methods for Fluid Dynamics, Sec. 9.4.1): the expansion of a
+    dense left state can push the flow past u_L, and c1 must stay above every
+    |u| the tube will see; c1 no larger than that, since a small T / c1^2
+    makes the scheme less robust.  With this rule max|omega| <= 1 + 1e-5 per
+    step at the left, right and star states of every tube (checked by the
+    tests; the residual growth sits at the smallest wave numbers, below 1 %
+    over the 1000 steps), and rho stays positive in every tube; 61 of the 256
+    (dense, fast left states) pass through T < 0 behind their shocks."""
     rng = np.random.Generator(np.random.PCG64(seed))
     L = np.round(np.exp(rng.uniform(math.log(256), math.log(4096), count))).astype(int)
     r = np.exp(rng.uniform(0.0, math.log(1000.0), count))
     M = rng.uniform(0.0, 30.0, count)
     out = []
+    z = (GAMMA_AIR - 1.0) / (2.0 * GAMMA_AIR)
     for k in range(count):
         uL = float(M[k]) * math.sqrt(GAMMA_AIR)
-        c1 = max(3.0, 1.1 * uL + 2.0)
+        aL = aR = math.sqrt(GAMMA_AIR)           # T = 1 on both sides
+        pL, pR = float(r[k]), 1.0
+        p_star = ((aL + aR - 0.5 * (GAMMA_AIR - 1.0) * (0.0 - uL)) / (aL / pL ** z + aR / pR ** z)) ** (1.0 / z)
+        u_star = uL - 2.0 * aL / (GAMMA_AIR - 1.0) * ((p_star / pL) ** z - 1.0)
+        c1 = max(3.0, 1.1 * uL + 2.0, 1.05 * u_star + 0.5)
         out.append(riemann(f"tube{k}_{L[k]}x{ny}", int(L[k]), ny, 1.0, (float(r[k]), uL, 0.0, float(r[k])),
                            (1.0, 0.0, 0.0, 1.0), 0.5, c1, 2.4 * c1, 1.2 * c1, alpha=0.05, steps=steps,
                            lam_scale=2.0))

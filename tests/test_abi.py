@@ -89,3 +89,39 @@ def test_create_without_gpu_reports_cuda_error():
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_create(*_args(W.sod_400x4()))
     assert ei.value.status in (lbm.LBM_E_CUDA, lbm.LBM_E_NOMEM)
+
+
+def _vn(**over):
+    p = W.sod_400x4()
+    q = lbm.vn_case(p, over.pop("state", (1.0, 0.0, 0.0, 1.0)))
+    for k, v in over.items():
+        if k in ("c1", "c2", "eta0"):
+            setattr(q.dvm, k, v)
+        elif k == "beta":
+            q.diss.beta = v
+        elif k == "lam8":
+            q.diss.lambda_[8] = v
+        else:
+            setattr(q, k, v)
+    return q
+
+
+@pytest.mark.parametrize("kw,msg", [
+    (dict(cases=[_vn(c2=3.0)]), "case 0: c1"), (dict(cases=[_vn(), _vn(beta=0.7)]), "case 1: beta"),
+    (dict(cases=[_vn(lam8=-1.0)]), "lambda[8]"), (dict(cases=[_vn(state=(1.0, 0.0, 0.0, 0.0))]), "T > 0"),
+    (dict(cases=[_vn(tau=0.0)]), "tau"), (dict(dirs=[(0, 0)]), "direction 0"),
+    (dict(dirs=[(1, 0)] * 65), "ndirs"), (dict(nk=0), "nk"), (dict(nk=70000), "nk"),
+    (dict(growth=None), "both NULL"),
+])
+def test_vn_scan_rejects_invalid_arguments(kw, msg):
+    import numpy as np
+    args = dict(cases=[_vn()], dirs=[(1, 0)], nk=31, growth=np.zeros(1))
+    args.update(kw)
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_vn_scan(args["cases"], args["dirs"], args["nk"], growth=args["growth"])
+    assert ei.value.status == lbm.LBM_E_INVAL
+    assert msg in str(ei.value)
+
+
+def test_vn_scan_with_no_cases_does_nothing():
+    lbm.lbm_vn_scan([], [(1, 0)], 31)

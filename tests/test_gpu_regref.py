@@ -1,7 +1,17 @@
 """The steady regular reflection of a 30-degree Mach-10 shock (Sec. 4.2,
 Fig. 11, Eq. Riemann-3) on the GPU: the three states and both shock lines
 against the exact oblique-shock solution, and a reduced grid against the
-oracle."""
+oracle.
+
+The tolerances come from the FP64 oracle's own convergence on this problem
+(dx = 0.05, 0.025, 0.01): the incident shock leaves the inflow corner
+0.087, 0.063, 0.043 upstream of the exact line at angles 30.56, 30.62,
+30.15 degrees, and the mean density behind it is 2.6 %, 1.5 %, 0.7 % below
+the exact 5.  At dx = 0.01 the reflected shock crosses x = 8 about one cell
+above the exact point and the density behind it is within 0.5 % of the
+exact value away from the wall; the rows next to the wall (y < 0.25) carry
+a denser layer (up to 5 %) that starts at the reflection point, so the state
+checks leave them out."""
 import math
 
 import numpy as np
@@ -14,42 +24,54 @@ from paper_0706_0405_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu
 G = 1.4
+ROWS = np.array([2.5, 2.25, 2.0, 1.75, 1.5, 1.25, 1.0, 0.75])
 
 
 def _exact():
+    """Densities of regions 1-3, the wall point of the incident shock and the
+    slope of the reflected shock line (weak oblique-shock solution for the
+    turn that brings the flow behind the incident shock back along the wall)."""
     p = W.regular_reflection()
-    top = p.sides[3].state_lo
-    r, u, v, T = top
+    r, u, v, T = p.sides[3].state_lo
     ref = gd.oblique_shock_for_turn(r, u, v, r * T, -math.atan2(v, u), G)
-    x_reflect = 3.0 / math.tan(math.pi / 6)                 # incident shock meets the wall
-    slope_reflected = math.tan(math.atan2(v, u) + ref[4])    # reflected shock line
-    return p, (1.0, r, ref[0]), x_reflect, slope_reflected
+    x_wall = 3.0 / math.tan(math.pi / 6)
+    slope = math.tan(math.atan2(v, u) + ref[4])
+    return p, (1.0, r, ref[0]), x_wall, slope
 
 
-def _index(coord, dx):
-    return int(round(coord / dx - 0.5))
+def _crossing(profile, level, dx):
+    """Position (cell centres at (k + 1/2) dx) where the profile first rises
+    through ``level``, by linear interpolation between the two cells."""
+    k = int(np.argmax(profile > level))
+    return (k - 0.5 + (level - profile[k - 1]) / (profile[k] - profile[k - 1])) * dx
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_tdf"])
 def test_regular_reflection_matches_exact_solution(prec):
-    p, rho, x_ref, slope = _exact()
+    p, rho, x_wall, slope = _exact()
     with lbm.Lattice(p, prec) as lat:
         lat.init(*W.initial_fields(p)).step(p.steps)
         lat.sync()
         r = lat.moments()[0].double().cpu().numpy()
     dx = p.dx
-    # region 1 (inflow), 2 (behind the incident shock), 3 (behind the reflected one)
-    assert r[_index(0.5, dx), _index(2.0, dx)] == pytest.approx(rho[0], rel=0.01)
-    assert r[_index(2.5, dx), _index(3.0, dx)] == pytest.approx(rho[1], rel=0.02)
-    assert r[_index(0.3, dx), _index(8.0, dx)] == pytest.approx(rho[2], rel=0.03)
-    # incident shock along y = 1.5: exact x = 1.5 / tan 30
-    row = r[_index(1.5, dx)]
-    x_inc = (np.argmax(row > 0.5 * (rho[0] + rho[1])) + 0.5) * dx
-    assert abs(x_inc - 1.5 / math.tan(math.pi / 6)) <= 3 * dx
-    # reflected shock along x = 8: exact y = (8 - x_reflect) tan(angle)
-    col = r[:, _index(8.0, dx)]
-    y_ref = (np.argmax(col < 0.5 * (rho[1] + rho[2])) + 0.5) * dx
-    assert abs(y_ref - (8.0 - x_ref) * slope) <= 4 * dx
+    X, Y = np.meshgrid((np.arange(p.nx) + 0.5) * dx, (np.arange(p.ny) + 0.5) * dx)
+    x_inc = lambda y: (3.0 - y) / math.tan(math.pi / 6)
+    # incident shock: straight, at 30 degrees, near the exact line
+    xs = np.array([_crossing(r[int(y / dx)], 0.5 * (rho[0] + rho[1]), dx) for y in ROWS])
+    fit = np.polyfit(ROWS, xs, 1)
+    assert abs(math.degrees(math.atan(-1.0 / fit[0])) - 30.0) <= 0.5
+    assert np.max(np.abs(xs - x_inc(ROWS))) <= 0.1
+    # states: inflow, behind the incident shock, behind the reflected one
+    m1 = (X < x_inc(Y) - 0.5) & (Y > 0.75) & (Y < 2.5)
+    m2 = (X > x_inc(Y) + 0.3) & (Y > 1.5) & (X < 7.0)
+    m3 = (X > 7.5) & (Y > 0.25) & (Y < 0.45)
+    assert np.max(np.abs(r[m1] - rho[0])) <= 0.02 * rho[0]
+    assert abs(r[m2].mean() - rho[1]) <= 0.015 * rho[1]
+    assert abs(r[m3].mean() - rho[2]) <= 0.015 * rho[2]
+    # reflected shock crossing the column x = 8
+    col = r[:, int(8.0 / dx)][::-1]       # from the top down, density rises through it
+    y_ref = p.ny * dx - _crossing(col, 0.5 * (rho[1] + rho[2]), dx)
+    assert abs(y_ref - (8.0 - x_wall) * slope) <= 4 * dx
 
 
 def test_regular_reflection_reduced_grid_matches_oracle_fp64():
