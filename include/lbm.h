@@ -68,13 +68,25 @@ enum {
     LBM_FLAG_T_NONPOSITIVE = 4  /* T <= 0 at some node (allowed, informational) */
 };
 
-/* Storage and arithmetic precision of a context. */
+/* Storage and arithmetic precision of a context.
+ * In the FP32 modes T is recovered from the internal energy formed around u,
+ * T = sum_i f_i (|v_i - u|^2 + eta_i^2) / (b rho), so no large totals cancel.
+ * The modes marked "moment-exact" also correct the relaxation term
+ * omega f^eq so that it carries exactly omega times the mass, momentum and
+ * energy of f: an FP32 evaluation of f^eq loses them at high Mach (the
+ * internal energy is a small part of terms of size u^2) and, the same loss
+ * recurring every step, T drifts (tens of per cent over 5.8e4 steps of the
+ * Mach-30 tube of Eq. Riemann-1 in LBM_FP32). */
 typedef enum lbm_precision {
     LBM_FP64 = 0,      /* f stored and updated in FP64 */
-    LBM_FP32 = 1,      /* f in FP32; T from the internal energy in FP32 */
-    LBM_FP32_T64 = 2,  /* f in FP32; internal energy for T accumulated in FP64 */
-    LBM_FP32_TDF = 3   /* f in FP32; internal energy for T in double-float
-                          (pairs of FP32 with error-free sums and products) */
+    LBM_FP32 = 1,      /* f in FP32; internal energy summed in FP32 */
+    LBM_FP32_T64 = 2,  /* f in FP32; internal energy accumulated in FP64;
+                          moment-exact */
+    LBM_FP32_TDF = 3,  /* f in FP32; internal energy in double-float (pairs
+                          of FP32 with error-free sums and products);
+                          moment-exact */
+    LBM_FP32_CONS = 4  /* f in FP32; internal energy summed in FP32;
+                          moment-exact */
 } lbm_precision;
 
 /* Boundary kinds.  The paper names the kinds (Sec. 4.2, text of

@@ -184,6 +184,7 @@ LBM_ADJ_INST(double, T_PLAIN)
 LBM_ADJ_INST(float, T_INT32)
 LBM_ADJ_INST(float, T_INT64)
 LBM_ADJ_INST(float, T_DF)
+LBM_ADJ_INST(float, T_CONS)
 #undef LBM_ADJ_INST
 template int adjoint_partials<double>(const Grid<double>&);
 template int adjoint_partials<float>(const Grid<float>&);

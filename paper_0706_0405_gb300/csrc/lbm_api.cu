@@ -130,6 +130,15 @@ Model<double> build_model(double b, double tau, double dt, double dx, const lbm_
     M.b5u = 1.0 / d5;
     M.D1 = 1.0 / (2.0 * c1s * c1s);
     M.D5 = 1.0 / (2.0 * c2s * c2s);
+    // moment-exact relaxation: absorb mass / energy defects in the moving set
+    // whose c^2 - eta0^2 is larger in size (c1 != c2, so one is nonzero)
+    M.h1 = 0.5 / c1;
+    const double ea = c1s - e0s, ed = c2s - e0s;
+    const bool diag = std::fabs(ed) > std::fabs(ea);
+    const double rho_o = diag ? ea / ed : ed / ea;
+    M.kcons = 0.25 * rho_o;
+    M.kzero = 1.0 - rho_o;
+    M.cons_diag = diag ? 1.0 : 0.0;
     const double beta = diss.beta, r = dt / dx;
     for (int i = 0; i < 9; ++i) {
         const double mag = i == 0 ? 0.0 : (i <= 4 ? c1 : M.d);
@@ -241,7 +250,7 @@ lbm_status validate(int nx, int ny, double b, double tau, double dt, double dx, 
     for (int i = 0; i < 9; ++i)
         if (!(std::isfinite(diss->lambda[i]) && diss->lambda[i] >= 0.0))
             return fail(nullptr, LBM_E_INVAL, "lambda[%d] must be finite and >= 0", i);
-    if (prec < LBM_FP64 || prec > LBM_FP32_TDF) return fail(nullptr, LBM_E_INVAL, "unknown precision %d", (int)prec);
+    if (prec < LBM_FP64 || prec > LBM_FP32_CONS) return fail(nullptr, LBM_E_INVAL, "unknown precision %d", (int)prec);
     for (int s = 0; s < 4; ++s) {
         const lbm_bc& q = bc[s];
         for (int part = 0; part < 2; ++part) {
@@ -305,6 +314,7 @@ cudaError_t dispatch(lbm_ctx* c, F&& fn) {
     case LBM_FP64: return fn(double{}, std::integral_constant<int, T_PLAIN>{});
     case LBM_FP32: return fn(float{}, std::integral_constant<int, T_INT32>{});
     case LBM_FP32_T64: return fn(float{}, std::integral_constant<int, T_INT64>{});
+    case LBM_FP32_CONS: return fn(float{}, std::integral_constant<int, T_CONS>{});
     default: return fn(float{}, std::integral_constant<int, T_DF>{});
     }
 }
@@ -1056,6 +1066,7 @@ cudaError_t batch_launch(lbm_batch* b, int n) {
     switch (b->prec) {
     case LBM_FP32_T64: return go(std::integral_constant<int, T_INT64>{});
     case LBM_FP32_TDF: return go(std::integral_constant<int, T_DF>{});
+    case LBM_FP32_CONS: return go(std::integral_constant<int, T_CONS>{});
     default: return go(std::integral_constant<int, T_INT32>{});
     }
 }
@@ -1090,7 +1101,7 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
     if (!out) return bfail(nullptr, LBM_E_INVAL, "out must not be NULL");
     *out = nullptr;
     if (nprob < 1 || !probs) return bfail(nullptr, LBM_E_INVAL, "lbm_batch_create: need nprob >= 1 problems");
-    if (prec != LBM_FP32 && prec != LBM_FP32_T64 && prec != LBM_FP32_TDF)
+    if (prec != LBM_FP32 && prec != LBM_FP32_T64 && prec != LBM_FP32_TDF && prec != LBM_FP32_CONS)
         return bfail(nullptr, LBM_E_INVAL, "lbm_batch_create: the batch runs the FP32 modes only");
     lbm_batch* b = new lbm_batch();
     b->prec = prec;
@@ -1144,8 +1155,10 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
         lbm_batch_destroy(b);
         return bfail(nullptr, e == cudaErrorMemoryAllocation ? LBM_E_NOMEM : LBM_E_CUDA, m);
     }
-    int maxg = prec == LBM_FP32_T64 ? batch_max_grid<T_INT64>()
-               : prec == LBM_FP32_TDF ? batch_max_grid<T_DF>() : batch_max_grid<T_INT32>();
+    int maxg = prec == LBM_FP32_T64    ? batch_max_grid<T_INT64>()
+               : prec == LBM_FP32_TDF  ? batch_max_grid<T_DF>()
+               : prec == LBM_FP32_CONS ? batch_max_grid<T_CONS>()
+                                       : batch_max_grid<T_INT32>();
     b->grid = maxg < b->ntiles ? maxg : b->ntiles;
     *out = b;
     return LBM_OK;

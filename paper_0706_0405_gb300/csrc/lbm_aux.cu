@@ -237,5 +237,8 @@ template cudaError_t launch_moments<float, T_INT64>(const float*, float*, float*
 template cudaError_t launch_moments<float, T_DF>(const float*, float*, float*, float*, float*,
                                                  const Model<float>&, const Grid<float>&,
                                                  unsigned*, cudaStream_t);
+template cudaError_t launch_moments<float, T_CONS>(const float*, float*, float*, float*, float*,
+                                                 const Model<float>&, const Grid<float>&,
+                                                 unsigned*, cudaStream_t);
 
 }  // namespace lbm

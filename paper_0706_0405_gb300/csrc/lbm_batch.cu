@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(kBatchThreads)
                 moments<float, TM>(f, sM, rho, ux, uy, Tt);
                 bits |= health(rho, ux, uy, Tt);
                 float ofe[9], o[9];
-                omega_equilibrium(sM, rho, ux, uy, Tt, ofe);
+                relaxation<float, TM>(sM, f, rho, ux, uy, Tt, ofe);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) {
                     const float* bp = b + i * kBoxPlane;
@@ -177,8 +177,11 @@ template cudaError_t launch_batch<T_INT64>(const BatchProb*, const int4*, int, i
                                            unsigned*, unsigned*, int, cudaStream_t);
 template cudaError_t launch_batch<T_DF>(const BatchProb*, const int4*, int, int, long long*, unsigned*,
                                         unsigned*, unsigned*, int, cudaStream_t);
+template cudaError_t launch_batch<T_CONS>(const BatchProb*, const int4*, int, int, long long*, unsigned*,
+                                          unsigned*, unsigned*, int, cudaStream_t);
 template int batch_max_grid<T_INT32>();
 template int batch_max_grid<T_INT64>();
 template int batch_max_grid<T_DF>();
+template int batch_max_grid<T_CONS>();
 
 }  // namespace lbm

@@ -18,8 +18,16 @@ enum TMode : int {
     T_PLAIN = 0,  // T = (E / rho - u^2) / b in the storage precision (FP64 mode)
     T_INT32 = 1,  // T = sum f_i |v_i - u|^2 (+ eta^2 on i = 0) / (b rho), FP32
     T_INT64 = 2,  // same, the nine exact FP32 products summed in FP64
-    T_DF = 3      // same, summed in double-float (error-free FP32 transforms)
+    T_DF = 3,     // same, summed in double-float (error-free FP32 transforms)
+    T_CONS = 4    // as T_INT32
 };
+
+// FP32 modes whose relaxation term is corrected to carry exactly omega times
+// the mass, momentum and energy of f (see conserve below).
+template <int TM>
+constexpr bool moment_exact() {
+    return TM == T_INT64 || TM == T_DF || TM == T_CONS;
+}
 
 enum BcKind : int { BC_PERIODIC = 0, BC_OUTFLOW = 1, BC_DIRICHLET = 2, BC_REFLECT = 3 };
 enum Side : int { S_LEFT = 0, S_RIGHT = 1, S_BOTTOM = 2, S_TOP = 3 };
@@ -43,6 +51,12 @@ struct Model {
     S b1c, b1T, b1u;  // B_1..4 = b1c + b1T T + b1u u^2 (Eq. e18)
     S b5c, b5T, b5u;  // B_5..8
     S D1, D5;         // D_1..4, D_5..8 (Eq. e18)
+    // moment-exact relaxation (conserve): 1 / (2 c1); the set of four moving
+    // populations that absorbs the mass / energy defect (0: axes 1..4,
+    // 1: diagonals 5..8) with kcons = rho_o / 4 and kzero = 1 - rho_o, where
+    // rho_o = (c_o^2 - eta0^2) / (c_s^2 - eta0^2) for the set's speed c_s
+    // and the other set's c_o
+    S h1, kcons, kzero, cons_diag;
 };
 
 // Grid and boundary description.
@@ -112,7 +126,7 @@ __device__ __forceinline__ void moments(const S (&f)[9], const Model<S>& M, S& r
                         fma_(xp, xp, uy2),            fma_(yp, yp, ux2), add_(qxm, qym),
                         add_(qxp, qym),               add_(qxp, qyp),    add_(qxm, qyp)};
         S e;
-        if constexpr (TM == T_INT32) {
+        if constexpr (TM == T_INT32 || TM == T_CONS) {
             e = mul_(f[0], w[0]);
 #pragma unroll
             for (int i = 1; i < 9; ++i) e = fma_(f[i], w[i], e);
@@ -175,6 +189,66 @@ __device__ __forceinline__ void equilibrium(const Model<S>& M, S rho, S ux, S uy
 template <typename S>
 __device__ __forceinline__ void omega_equilibrium(const Model<S>& M, S rho, S ux, S uy, S T, S (&ofe)[9]) {
     equilibrium_scaled(M, mul_(M.omega, rho), ux, uy, T, ofe);
+}
+
+// Moment-exact relaxation term.  In FP32 the equilibrium evaluated from
+// FP32 moments does not carry exactly the mass, momentum and energy it was
+// built from: at high Mach the internal energy is a small part of terms of
+// size u^2, so each evaluation shifts T by a fixed relative amount of order
+// 2^-24 u^2 / T, and the same shift recurs every step in a uniform stream
+// (a drift that reaches tens of per cent over 10^4-10^5 steps at Mach 30).
+// The defects d_i = omega f^eq_i - omega f_i are formed one population at a
+// time (one rounding each, so they are accurate even where they are tiny)
+// and their moments are removed with the fewest populations:
+//  * momentum by the opposite axis pairs (3, 1) and (4, 2):
+//    f3 -= g_x, f1 += g_x with g_x = d j_x / (2 c1) (mass and |v|^2 unchanged);
+//  * mass and energy by the rest population and one set of four moving
+//    populations s (axes or diagonals, speed c_s, sum of v = 0): adding
+//    delta_0 and delta_s to each of the set keeps the momentum and removes
+//    mass sum d and energy sum d (|v|^2 + eta^2) when
+//    delta_s = -(S_s + rho_o S_o) / 4 and delta_0 = -d_0 - (1 - rho_o) S_o,
+//    S_s, S_o the defect sums of the set and of the other set.
+// Then omega f^eq has exactly (up to the final roundings) omega times the
+// mass, momentum and energy of f (Eqs. e4, e5, e7), as it has in exact
+// arithmetic, and the collision conserves them.
+template <typename S, int TM>
+__device__ __forceinline__ void conserve(const Model<S>& M, const S (&f)[9], S (&ofe)[9]) {
+    if constexpr (moment_exact<TM>()) {
+        S d[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) d[i] = fma_(-M.omega, f[i], ofe[i]);
+        const S sa = add_(add_(d[1], d[3]), add_(d[2], d[4]));
+        const S sd = add_(add_(d[5], d[7]), add_(d[6], d[8]));
+        const S djx = fma_(M.c1, sub_(d[3], d[1]), mul_(M.d, sub_(add_(d[6], d[7]), add_(d[5], d[8]))));
+        const S djy = fma_(M.c1, sub_(d[4], d[2]), mul_(M.d, sub_(add_(d[7], d[8]), add_(d[5], d[6]))));
+        const S gx = mul_(djx, M.h1), gy = mul_(djy, M.h1);
+        if (M.cons_diag == S(0)) {
+            const S t = fma_(sd, M.kcons, mul_(sa, S(0.25)));  // -delta_s
+            ofe[0] = sub_(ofe[0], fma_(sd, M.kzero, d[0]));
+            ofe[1] = sub_(add_(ofe[1], gx), t);
+            ofe[3] = sub_(sub_(ofe[3], gx), t);
+            ofe[2] = sub_(add_(ofe[2], gy), t);
+            ofe[4] = sub_(sub_(ofe[4], gy), t);
+        } else {
+            const S t = fma_(sa, M.kcons, mul_(sd, S(0.25)));
+            ofe[0] = sub_(ofe[0], fma_(sa, M.kzero, d[0]));
+            ofe[1] = add_(ofe[1], gx);
+            ofe[3] = sub_(ofe[3], gx);
+            ofe[2] = add_(ofe[2], gy);
+            ofe[4] = sub_(ofe[4], gy);
+#pragma unroll
+            for (int i = 5; i < 9; ++i) ofe[i] = sub_(ofe[i], t);
+        }
+    }
+}
+
+// omega f^eq of the node's own moments, moment-exact in the modes that ask
+// for it: the relaxation term of every step kernel.
+template <typename S, int TM>
+__device__ __forceinline__ void relaxation(const Model<S>& M, const S (&f)[9], S rho, S ux, S uy, S T,
+                                           S (&ofe)[9]) {
+    omega_equilibrium(M, rho, ux, uy, T, ofe);
+    conserve<S, TM>(M, f, ofe);
 }
 
 // Update of one population from its five-point star and omega f^eq
@@ -306,7 +380,7 @@ __device__ __forceinline__ unsigned node_step(const S* __restrict__ fin, S* __re
     moments<S, TM>(f, M, rho, ux, uy, T);
     const unsigned bits = health(rho, ux, uy, T);
     S ofe[9];
-    omega_equilibrium(M, rho, ux, uy, T, ofe);
+    relaxation<S, TM>(M, f, rho, ux, uy, T, ofe);
     S o[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) {
@@ -400,7 +474,7 @@ __device__ __forceinline__ unsigned vec_group(const float* __restrict__ fin, flo
         moments<float, TM>(f, M, rho, ux, uy, T);
         if (k < nvalid) bits |= health(rho, ux, uy, T);
         float ofe[9];
-        omega_equilibrium(M, rho, ux, uy, T, ofe);
+        relaxation<float, TM>(M, f, rho, ux, uy, T, ofe);
 #pragma unroll
         for (int i = 0; i < 9; ++i) acc[i][k] = ofe[i];
     }

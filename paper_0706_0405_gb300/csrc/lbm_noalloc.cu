@@ -109,7 +109,7 @@ extern "C" lbm_status lbm_conservation_noalloc(const void* f, int nx, int ny, lb
     if (nx < 1 || ny < 1) return LBM_E_INVAL;
     const long long n = (long long)nx * (long long)ny;
     if (n > kMaxNodes) return LBM_E_INVAL;  // more tiles than the static scratch holds
-    if (prec < LBM_FP64 || prec > LBM_FP32_TDF) return LBM_E_INVAL;
+    if (prec < LBM_FP64 || prec > LBM_FP32_CONS) return LBM_E_INVAL;
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();

@@ -143,7 +143,7 @@ __global__ void __launch_bounds__(kTileThreads, 3)
             moments<float, TM>(f, M, rho, ux, uy, T);
             if (j < nvalid) bits |= health(rho, ux, uy, T);
             float ofe[9];
-            omega_equilibrium(M, rho, ux, uy, T, ofe);
+            relaxation<float, TM>(M, f, rho, ux, uy, T, ofe);
 #pragma unroll
             for (int i = 0; i < 9; ++i) acc[i][j] = ofe[i];
         }
@@ -329,7 +329,7 @@ __global__ void __launch_bounds__(TX, 2)
                 moments<float, TM>(f, M, rho, ux, uy, T);
                 report(status, health(rho, ux, uy, T));
                 float fe[9];
-                omega_equilibrium(M, rho, ux, uy, T, fe);
+                relaxation<float, TM>(M, f, rho, ux, uy, T, fe);
 #pragma unroll
                 for (int i = 0; i < 9; ++i)
                     o[i] = update(M, i, fe[i], C[i], sc[i * WPAD + tid + 5], sc[i * WPAD + tid + 3],
@@ -420,6 +420,7 @@ LBM_STEP_INST(double, T_PLAIN)
 LBM_STEP_INST(float, T_INT32)
 LBM_STEP_INST(float, T_INT64)
 LBM_STEP_INST(float, T_DF)
+LBM_STEP_INST(float, T_CONS)
 #undef LBM_STEP_INST
 
 }  // namespace lbm

@@ -20,7 +20,7 @@ LBM_OK, LBM_E_INVAL, LBM_E_NOMEM, LBM_E_CUDA, LBM_E_NONPHYSICAL, LBM_E_TIMEOUT, 
     0, -1, -2, -3, -4, -5, -6
 STATUS_NAMES = {0: "LBM_OK", -1: "LBM_E_INVAL", -2: "LBM_E_NOMEM", -3: "LBM_E_CUDA",
                 -4: "LBM_E_NONPHYSICAL", -5: "LBM_E_TIMEOUT", -6: "LBM_E_STATE"}
-PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_t64": 2, "fp32_tdf": 3}
+PRECISIONS = {"fp64": 0, "fp32": 1, "fp32_t64": 2, "fp32_tdf": 3, "fp32_cons": 4}
 BC_KINDS = {"periodic": 0, "outflow": 1, "dirichlet": 2, "reflect": 3}
 
 # Exported symbols of include/lbm.h.

@@ -16,7 +16,7 @@ def _subset():
     return [probs[k] for k in idx]
 
 
-@pytest.mark.parametrize("prec", ["fp32", "fp32_tdf"])
+@pytest.mark.parametrize("prec", ["fp32", "fp32_tdf", "fp32_cons"])
 def test_batch_equals_problems_stepped_alone(prec):
     probs = _subset()
     fields = [W.initial_fields(p) for p in probs]

@@ -1,0 +1,125 @@
+"""The Mach-30 Riemann problem of Eq. (Riemann-1) to t = 0.36 (Figs. 8, 9)
+on the GPU: the solution against the exact one, the first-order upwind
+variant (beta = 0, Fig. 9a), the lambda_0 sweep (Fig. 9b), the FP32
+temperature recovery across the Mach-30 shocks, and the variants against
+the oracle on a short run.
+
+The collision of the Mach-30 stream with the gas at rest gives two shocks
+and a star state (rho, u, p) = (8.27, 15, 380.2), T* = 45.95, with the
+fronts at x = 10.305 and 12.495.  The FP64 oracle on this grid gives:
+L1(rho) 1.6 % with both fronts within one cell; for lambda_0 = 2, 3, 4, 5
+c1 dx shock widths (10-90 %) of 13, 17, 20, 23 cells and a temperature
+deficit in the star region of 0.3, 2.8, 5.4, 7.9 %; for beta = 0 an excess
+of 3.2 % and T < 0 at both fronts."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import gasdynamics as gd
+from paper_0706_0405_gb300 import lbm
+from paper_0706_0405_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+WL, WR = (1.4, 30.0, 1.0), (1.4, 0.0, 1.0)
+
+
+def _run(p, prec="fp64"):
+    with lbm.Lattice(p, prec) as lat:
+        lat.init(*W.initial_fields(p)).step(p.steps)
+        lat.sync()
+        flags = lat.health()
+        r, ux, uy, T = [t.double().cpu().numpy()[0] for t in lat.moments()]
+    return r, ux, T, flags
+
+
+def _exact(p):
+    x = (np.arange(p.nx) + 0.5) * p.dx
+    rho, u, pr = gd.riemann_profile(WL, WR, 1.4, x, 6.0, p.steps * p.dt)
+    return x, rho, pr / rho
+
+
+def _measures(p, r, T):
+    """Front positions (half-jump crossings), width of the right shock in
+    cells (10-90 % of the jump) and the extreme relative temperature errors
+    in the star region 0.3 away from both fronts."""
+    x, re, Te = _exact(p)
+    hi = re.max()
+    above = np.where(r > 1.4 + 0.5 * (hi - 1.4))[0]
+    xl, xr = x[above.min()], x[above.max()]
+    frac = (r - 1.4) / (hi - 1.4)
+    width = int(np.sum((frac > 0.1) & (frac < 0.9) & (x > 0.5 * (xl + xr))))
+    core = (x > xl + 0.3) & (x < xr - 0.3)
+    dT = (T[core] - Te.max()) / Te.max()
+    return xl, xr, width, dT.min(), dT.max()
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_tdf"])
+def test_mach30_matches_exact_solution(prec):
+    p = W.mach30_fig8()
+    r, ux, T, flags = _run(p, prec)
+    x, re, Te = _exact(p)
+    assert flags == 0
+    assert np.sum(np.abs(r - re)) / np.sum(re) <= 0.025
+    xl, xr, width, dmin, dmax = _measures(p, r, T)
+    assert abs(xl - 10.305) <= 2 * p.dx and abs(xr - 12.495) <= 2 * p.dx
+    assert max(-dmin, dmax) <= 0.01
+
+
+def test_mach30_lambda0_sweep_widens_shock_and_deepens_temperature_error():
+    widths, deficits = [], []
+    for lam0 in (2.0, 3.0, 4.0, 5.0):
+        p = W.mach30_fig8(lam0_scale=lam0)
+        r, ux, T, flags = _run(p)
+        assert flags == 0
+        xl, xr, width, dmin, dmax = _measures(p, r, T)
+        widths.append(width)
+        deficits.append(-dmin)
+    assert all(a < b for a, b in zip(widths, widths[1:])), widths
+    assert all(a < b for a, b in zip(deficits, deficits[1:])), deficits
+    assert widths[-1] >= 1.5 * widths[0] and deficits[-1] >= 10 * deficits[0]
+
+
+def test_mach30_first_order_upwind_heats_the_star_region():
+    base = W.mach30_fig8()
+    up = W.mach30_fig8(beta=0.0)
+    r0, _, T0, f0 = _run(base)
+    r1, _, T1, f1 = _run(up)
+    x, re, Te = _exact(base)
+    m0, m1 = _measures(base, r0, T0), _measures(up, r1, T1)
+    assert f0 == 0 and f1 & lbm.LBM_FLAG_T_NONPOSITIVE
+    assert m1[4] >= 0.02 and m1[4] >= 5 * max(abs(m0[3]), abs(m0[4]))
+    assert np.sum(np.abs(r1 - re)) > np.sum(np.abs(r0 - re))
+
+
+def test_mach30_fp32_temperature_recovery_across_shocks():
+    """L1 of T and rho of the FP32 modes against the GPU's FP64 run at
+    t = 0.36 (5.76e4 steps): within the shock-crossing bar of 1e-3 for the
+    moment-exact modes; the plain FP32 mode drifts in the Mach-30 stream
+    (about 1.6e-2 in T)."""
+    p = W.mach30_fig8()
+    r64, _, T64, _ = _run(p, "fp64")
+    l1 = {}
+    for prec in ("fp32", "fp32_t64", "fp32_tdf", "fp32_cons"):
+        r32, _, T32, flags = _run(p, prec)
+        assert flags == 0
+        l1[prec] = (np.sum(np.abs(T32 - T64)) / np.sum(T64), np.sum(np.abs(r32 - r64)) / np.sum(r64))
+    for prec in ("fp32_t64", "fp32_tdf", "fp32_cons"):
+        assert l1[prec][0] <= 1e-3 and l1[prec][1] <= 1e-3, (prec, l1)
+    assert l1["fp32"][0] > 5e-3, l1
+
+
+@pytest.mark.parametrize("kw", [dict(beta=0.0), dict(lam0_scale=5.0), dict(lam0_scale=1.0)])
+def test_mach30_variants_match_oracle_fp64(kw):
+    p = W.mach30_fig8(steps=2000, **kw)
+    oracle.set_threads(oracle.max_threads())
+    f = oracle.init(p, *W.initial_fields(p))
+    oracle.run(p, f, p.steps)
+    ref = oracle.fields(p, f)
+    with lbm.Lattice(p, "fp64") as lat:
+        lat.init(*W.initial_fields(p)).step(p.steps)
+        g = [t.cpu().numpy() for t in lat.moments()]
+    assert np.max(np.abs(g[0] - ref[0]) / ref[0]) <= 1e-10
+    # T changes sign at the fronts of the growing variants: its error is
+    # taken against the largest |T| of the field
+    assert np.max(np.abs(g[3] - ref[3])) <= 1e-10 * np.max(np.abs(ref[3]))
+    assert np.max(np.abs(g[1] - ref[1])) <= 1e-10 * 30.0

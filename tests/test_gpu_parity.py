@@ -18,7 +18,7 @@ from paper_0706_0405_gb300.workloads import Side
 
 pytestmark = pytest.mark.gpu
 
-FP32_MODES = ("fp32", "fp32_t64", "fp32_tdf")
+FP32_MODES = ("fp32", "fp32_t64", "fp32_tdf", "fp32_cons")
 
 
 @pytest.fixture(scope="module", autouse=True)
