@@ -69,8 +69,9 @@ enum {
 };
 
 /* Storage and arithmetic precision of a context.
- * In the FP32 modes T is recovered from the internal energy formed around u,
- * T = sum_i f_i (|v_i - u|^2 + eta_i^2) / (b rho), so no large totals cancel.
+ * LBM_FP32, LBM_FP32_T64 and LBM_FP32_TDF recover T from the internal energy
+ * formed around u, T = sum_i f_i (|v_i - u|^2 + eta_i^2) / (b rho), so no
+ * large totals cancel.
  * The modes marked "moment-exact" also correct the relaxation term
  * omega f^eq so that it carries exactly omega times the mass, momentum and
  * energy of f: an FP32 evaluation of f^eq loses them at high Mach (the
@@ -85,8 +86,11 @@ typedef enum lbm_precision {
     LBM_FP32_TDF = 3,  /* f in FP32; internal energy in double-float (pairs
                           of FP32 with error-free sums and products);
                           moment-exact */
-    LBM_FP32_CONS = 4  /* f in FP32; internal energy summed in FP32;
-                          moment-exact */
+    LBM_FP32_CONS = 4  /* f in FP32; T = (E / rho - u^2) / b in FP32 (at
+                          high Mach its cancellation costs ~2^-24 u^2 / T
+                          relative in T, which only shapes the equilibrium:
+                          the mass, momentum and energy are kept by the
+                          moment-exact relaxation); moment-exact */
 } lbm_precision;
 
 /* Boundary kinds.  The paper names the kinds (Sec. 4.2, text of

@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+
 namespace lbm {
 
 // Interior column 0 sits at array column PADX, so that interior rows start on
@@ -19,7 +20,9 @@ enum TMode : int {
     T_INT32 = 1,  // T = sum f_i |v_i - u|^2 (+ eta^2 on i = 0) / (b rho), FP32
     T_INT64 = 2,  // same, the nine exact FP32 products summed in FP64
     T_DF = 3,     // same, summed in double-float (error-free FP32 transforms)
-    T_CONS = 4    // as T_INT32
+    T_CONS = 4    // T = (E / rho - u^2) / b in FP32 (with the moment-exact
+                  // relaxation its cancellation at high Mach only perturbs the
+                  // equilibrium's non-conserved part)
 };
 
 // FP32 modes whose relaxation term is corrected to carry exactly omega times
@@ -89,60 +92,74 @@ __device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b)
 __device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
 __device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
-// FP32: the hardware approximate reciprocal (about 1 ulp); the error of the
-// FP32 modes is set by the FP32 storage of f, far above that.
-__device__ __forceinline__ float rcp_(float a) { return __fdividef(1.0f, a); }
+// FP32: the hardware approximate reciprocal (PTX rcp.approx.ftz.f32, about
+// 1 ulp), issued as one instruction so that every kernel gets the same bits
+// whatever it does with the result; the error of the FP32 modes is set by
+// the FP32 storage of f, far above that.
+__device__ __forceinline__ float rcp_(float a) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(a));
+    return r;
+}
 __device__ __forceinline__ double add_(double a, double b) { return __dadd_rn(a, b); }
 __device__ __forceinline__ double sub_(double a, double b) { return __dsub_rn(a, b); }
 __device__ __forceinline__ double mul_(double a, double b) { return __dmul_rn(a, b); }
 __device__ __forceinline__ double fma_(double a, double b, double c) { return __fma_rn(a, b, c); }
 __device__ __forceinline__ double rcp_(double a) { return __drcp_rn(a); }
+__device__ __forceinline__ float neg_(float a) { return -a; }
+__device__ __forceinline__ double neg_(double a) { return -a; }
+
+// Internal energy sum_i f_i w_i with the nine exact FP32 products summed in
+// FP64.
+__device__ __forceinline__ float int64_energy(const float (&f)[9], const float (&w)[9]) {
+    double acc = __dmul_rn((double)f[0], (double)w[0]);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) acc = __fma_rn((double)f[i], (double)w[i], acc);
+    return (float)acc;
+}
 
 // ---------------------------------------------------------------- moments
 // rho = sum f (Eq. e4), rho u = sum f v (Eq. e5), T from Eq. (e7).
-template <typename S, int TM>
-__device__ __forceinline__ void moments(const S (&f)[9], const Model<S>& M, S& rho, S& ux, S& uy,
-                                        S& T) {
-    const S s14 = add_(add_(f[1], f[3]), add_(f[2], f[4]));
-    const S s58 = add_(add_(f[5], f[7]), add_(f[6], f[8]));
+template <typename S, int TM, typename V = S>
+__device__ __forceinline__ void moments(const V (&f)[9], const Model<S>& M, V& rho, V& ux, V& uy,
+                                        V& T) {
+    const V s14 = add_(add_(f[1], f[3]), add_(f[2], f[4]));
+    const V s58 = add_(add_(f[5], f[7]), add_(f[6], f[8]));
     rho = add_(add_(f[0], s14), s58);
-    const S jx = fma_(M.c1, sub_(f[3], f[1]), mul_(M.d, sub_(add_(f[6], f[7]), add_(f[5], f[8]))));
-    const S jy = fma_(M.c1, sub_(f[4], f[2]), mul_(M.d, sub_(add_(f[7], f[8]), add_(f[5], f[6]))));
-    const S inv = rcp_(rho);
+    const V jx = fma_(M.c1, sub_(f[3], f[1]), mul_(M.d, sub_(add_(f[6], f[7]), add_(f[5], f[8]))));
+    const V jy = fma_(M.c1, sub_(f[4], f[2]), mul_(M.d, sub_(add_(f[7], f[8]), add_(f[5], f[6]))));
+    const V inv = rcp_(rho);
     ux = mul_(jx, inv);
     uy = mul_(jy, inv);
-    if constexpr (TM == T_PLAIN) {
-        const S E = fma_(M.eta2, f[0], fma_(M.c1s, s14, mul_(M.c2s, s58)));
+    if constexpr (TM == T_PLAIN || TM == T_CONS) {
+        const V E = fma_(M.eta2, f[0], fma_(M.c1s, s14, mul_(M.c2s, s58)));
         T = mul_(sub_(mul_(E, inv), fma_(ux, ux, mul_(uy, uy))), M.inv_b);
     } else {
         // Internal energy sum_i f_i (|v_i - u|^2 + eta_i^2) = E - rho u^2; its
         // terms are formed around u, so the large totals never cancel, and an
         // error in u enters only at second order.
-        const S ux2 = mul_(ux, ux), uy2 = mul_(uy, uy);
-        const S xm = add_(M.c1, ux), xp = sub_(M.c1, ux), ym = add_(M.c1, uy), yp = sub_(M.c1, uy);
-        const S dxm = add_(M.d, ux), dxp = sub_(M.d, ux), dym = add_(M.d, uy), dyp = sub_(M.d, uy);
-        const S qxm = mul_(dxm, dxm), qxp = mul_(dxp, dxp), qym = mul_(dym, dym), qyp = mul_(dyp, dyp);
-        const S w[9] = {add_(M.eta2, add_(ux2, uy2)), fma_(xm, xm, uy2), fma_(ym, ym, ux2),
+        const V ux2 = mul_(ux, ux), uy2 = mul_(uy, uy);
+        const V xm = add_(M.c1, ux), xp = sub_(M.c1, ux), ym = add_(M.c1, uy), yp = sub_(M.c1, uy);
+        const V dxm = add_(M.d, ux), dxp = sub_(M.d, ux), dym = add_(M.d, uy), dyp = sub_(M.d, uy);
+        const V qxm = mul_(dxm, dxm), qxp = mul_(dxp, dxp), qym = mul_(dym, dym), qyp = mul_(dyp, dyp);
+        const V w[9] = {add_(M.eta2, add_(ux2, uy2)), fma_(xm, xm, uy2), fma_(ym, ym, ux2),
                         fma_(xp, xp, uy2),            fma_(yp, yp, ux2), add_(qxm, qym),
                         add_(qxp, qym),               add_(qxp, qyp),    add_(qxm, qyp)};
-        S e;
-        if constexpr (TM == T_INT32 || TM == T_CONS) {
+        V e;
+        if constexpr (TM == T_INT32) {
             e = mul_(f[0], w[0]);
 #pragma unroll
             for (int i = 1; i < 9; ++i) e = fma_(f[i], w[i], e);
         } else if constexpr (TM == T_INT64) {
-            double acc = __dmul_rn((double)f[0], (double)w[0]);
-#pragma unroll
-            for (int i = 1; i < 9; ++i) acc = __fma_rn((double)f[i], (double)w[i], acc);
-            e = (S)acc;
+            e = int64_energy(f, w);
         } else {  // T_DF: exact products p_i + q_i summed by TwoSum (Knuth)
-            float hi = 0.0f, lo = 0.0f;
+            V hi{}, lo{};  // +0 in every lane
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
-                const float p = mul_(f[i], w[i]);
-                const float q = fma_(f[i], w[i], -p);
-                const float s = add_(hi, p);
-                const float bb = sub_(s, hi);
+                const V p = mul_(f[i], w[i]);
+                const V q = fma_(f[i], w[i], neg_(p));
+                const V s = add_(hi, p);
+                const V bb = sub_(s, hi);
                 lo = add_(lo, add_(add_(sub_(hi, sub_(s, bb)), sub_(p, bb)), q));
                 hi = s;
             }
@@ -155,29 +172,34 @@ __device__ __forceinline__ void moments(const S (&f)[9], const Model<S>& M, S& r
 // Equilibrium of Eqs. (e16)-(e18) times a factor:
 // fe_i = scale (A_i + B_i v.u + D_i (v.u)^2); scale = rho gives f^eq, scale =
 // omega rho gives the relaxation term omega f^eq of the update directly.
-template <typename S>
-__device__ __forceinline__ void equilibrium_scaled(const Model<S>& M, S scale, S ux, S uy, S T, S (&fe)[9]) {
-    const S rho = scale;
-    const S u2 = fma_(ux, ux, mul_(uy, uy));
-    const S A1 = fma_(M.a1u, u2, fma_(M.a1T, T, M.a1c));
-    const S A5 = fma_(M.a5u, u2, fma_(M.a5T, T, M.a5c));
-    const S B1 = fma_(M.b1u, u2, fma_(M.b1T, T, M.b1c));
-    const S B5 = fma_(M.b5u, u2, fma_(M.b5T, T, M.b5c));
-    const S p = mul_(M.c1, ux), q = mul_(M.c1, uy);               // v.u of i = 3, 4 (-: 1, 2)
-    const S r = mul_(M.d, add_(ux, uy)), m = mul_(M.d, sub_(ux, uy));  // v.u of i = 7, 6 (-: 5, 8)
+template <typename S, typename V = S>
+__device__ __forceinline__ void equilibrium_scaled(const Model<S>& M, V scale, V ux, V uy, V T, V (&fe)[9]) {
+    const V rho = scale;
+    const V u2 = fma_(ux, ux, mul_(uy, uy));
     fe[0] = mul_(rho, mul_(M.k0, T));
-    // rho (A + D (v.u)^2) and rho B per group, then fe = rho (A + D (v.u)^2) +- rho B v.u
-    const S sp = mul_(rho, fma_(mul_(M.D1, p), p, A1)), sq = mul_(rho, fma_(mul_(M.D1, q), q, A1));
-    const S sr = mul_(rho, fma_(mul_(M.D5, r), r, A5)), sm = mul_(rho, fma_(mul_(M.D5, m), m, A5));
-    const S rB1 = mul_(rho, B1), rB5 = mul_(rho, B5);
-    fe[1] = fma_(-rB1, p, sp);
-    fe[3] = fma_(rB1, p, sp);
-    fe[2] = fma_(-rB1, q, sq);
-    fe[4] = fma_(rB1, q, sq);
-    fe[5] = fma_(-rB5, r, sr);
-    fe[7] = fma_(rB5, r, sr);
-    fe[6] = fma_(rB5, m, sm);
-    fe[8] = fma_(-rB5, m, sm);
+    // per group: rho (A + D (v.u)^2) and rho B, then fe = rho (A + D (v.u)^2) +- rho B v.u
+    {  // axes, v.u = +-p (i = 3, 1), +-q (i = 4, 2)
+        const V A1 = fma_(M.a1u, u2, fma_(M.a1T, T, M.a1c));
+        const V B1 = fma_(M.b1u, u2, fma_(M.b1T, T, M.b1c));
+        const V p = mul_(M.c1, ux), q = mul_(M.c1, uy);
+        const V sp = mul_(rho, fma_(mul_(M.D1, p), p, A1)), sq = mul_(rho, fma_(mul_(M.D1, q), q, A1));
+        const V rB1 = mul_(rho, B1);
+        fe[1] = fma_(neg_(rB1), p, sp);
+        fe[3] = fma_(rB1, p, sp);
+        fe[2] = fma_(neg_(rB1), q, sq);
+        fe[4] = fma_(rB1, q, sq);
+    }
+    {  // diagonals, v.u = +-r (i = 7, 5), +-m (i = 6, 8)
+        const V A5 = fma_(M.a5u, u2, fma_(M.a5T, T, M.a5c));
+        const V B5 = fma_(M.b5u, u2, fma_(M.b5T, T, M.b5c));
+        const V r = mul_(M.d, add_(ux, uy)), m = mul_(M.d, sub_(ux, uy));
+        const V sr = mul_(rho, fma_(mul_(M.D5, r), r, A5)), sm = mul_(rho, fma_(mul_(M.D5, m), m, A5));
+        const V rB5 = mul_(rho, B5);
+        fe[5] = fma_(neg_(rB5), r, sr);
+        fe[7] = fma_(rB5, r, sr);
+        fe[6] = fma_(rB5, m, sm);
+        fe[8] = fma_(neg_(rB5), m, sm);
+    }
 }
 
 template <typename S>
@@ -186,9 +208,9 @@ __device__ __forceinline__ void equilibrium(const Model<S>& M, S rho, S ux, S uy
 }
 
 // omega f^eq (the relaxation term of Eq. SEC-VON-11 with omega = dt / tau).
-template <typename S>
-__device__ __forceinline__ void omega_equilibrium(const Model<S>& M, S rho, S ux, S uy, S T, S (&ofe)[9]) {
-    equilibrium_scaled(M, mul_(M.omega, rho), ux, uy, T, ofe);
+template <typename S, typename V = S>
+__device__ __forceinline__ void omega_equilibrium(const Model<S>& M, V rho, V ux, V uy, V T, V (&ofe)[9]) {
+    equilibrium_scaled<S, V>(M, mul_(M.omega, rho), ux, uy, T, ofe);
 }
 
 // Moment-exact relaxation term.  In FP32 the equilibrium evaluated from
@@ -211,26 +233,26 @@ __device__ __forceinline__ void omega_equilibrium(const Model<S>& M, S rho, S ux
 // Then omega f^eq has exactly (up to the final roundings) omega times the
 // mass, momentum and energy of f (Eqs. e4, e5, e7), as it has in exact
 // arithmetic, and the collision conserves them.
-template <typename S, int TM>
-__device__ __forceinline__ void conserve(const Model<S>& M, const S (&f)[9], S (&ofe)[9]) {
+template <typename S, int TM, typename V = S>
+__device__ __forceinline__ void conserve(const Model<S>& M, const V (&f)[9], V (&ofe)[9]) {
     if constexpr (moment_exact<TM>()) {
-        S d[9];
+        V d[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) d[i] = fma_(-M.omega, f[i], ofe[i]);
-        const S sa = add_(add_(d[1], d[3]), add_(d[2], d[4]));
-        const S sd = add_(add_(d[5], d[7]), add_(d[6], d[8]));
-        const S djx = fma_(M.c1, sub_(d[3], d[1]), mul_(M.d, sub_(add_(d[6], d[7]), add_(d[5], d[8]))));
-        const S djy = fma_(M.c1, sub_(d[4], d[2]), mul_(M.d, sub_(add_(d[7], d[8]), add_(d[5], d[6]))));
-        const S gx = mul_(djx, M.h1), gy = mul_(djy, M.h1);
+        const V sa = add_(add_(d[1], d[3]), add_(d[2], d[4]));
+        const V sd = add_(add_(d[5], d[7]), add_(d[6], d[8]));
+        const V djx = fma_(M.c1, sub_(d[3], d[1]), mul_(M.d, sub_(add_(d[6], d[7]), add_(d[5], d[8]))));
+        const V djy = fma_(M.c1, sub_(d[4], d[2]), mul_(M.d, sub_(add_(d[7], d[8]), add_(d[5], d[6]))));
+        const V gx = mul_(djx, M.h1), gy = mul_(djy, M.h1);
         if (M.cons_diag == S(0)) {
-            const S t = fma_(sd, M.kcons, mul_(sa, S(0.25)));  // -delta_s
+            const V t = fma_(sd, M.kcons, mul_(sa, S(0.25)));  // -delta_s
             ofe[0] = sub_(ofe[0], fma_(sd, M.kzero, d[0]));
             ofe[1] = sub_(add_(ofe[1], gx), t);
             ofe[3] = sub_(sub_(ofe[3], gx), t);
             ofe[2] = sub_(add_(ofe[2], gy), t);
             ofe[4] = sub_(sub_(ofe[4], gy), t);
         } else {
-            const S t = fma_(sa, M.kcons, mul_(sd, S(0.25)));
+            const V t = fma_(sa, M.kcons, mul_(sd, S(0.25)));
             ofe[0] = sub_(ofe[0], fma_(sa, M.kzero, d[0]));
             ofe[1] = add_(ofe[1], gx);
             ofe[3] = sub_(ofe[3], gx);
@@ -244,18 +266,18 @@ __device__ __forceinline__ void conserve(const Model<S>& M, const S (&f)[9], S (
 
 // omega f^eq of the node's own moments, moment-exact in the modes that ask
 // for it: the relaxation term of every step kernel.
-template <typename S, int TM>
-__device__ __forceinline__ void relaxation(const Model<S>& M, const S (&f)[9], S rho, S ux, S uy, S T,
-                                           S (&ofe)[9]) {
-    omega_equilibrium(M, rho, ux, uy, T, ofe);
-    conserve<S, TM>(M, f, ofe);
+template <typename S, int TM, typename V = S>
+__device__ __forceinline__ void relaxation(const Model<S>& M, const V (&f)[9], V rho, V ux, V uy, V T,
+                                           V (&ofe)[9]) {
+    omega_equilibrium<S, V>(M, rho, ux, uy, T, ofe);
+    conserve<S, TM, V>(M, f, ofe);
 }
 
 // Update of one population from its five-point star and omega f^eq
 // (Eq. SEC-VON-11 with the folded weights of Model::w).
-template <typename S>
-__device__ __forceinline__ S update(const Model<S>& M, int i, S ofe, S c, S e, S w, S n, S s) {
-    S acc = fma_(M.w[i][0], c, ofe);
+template <typename S, typename V = S>
+__device__ __forceinline__ V update(const Model<S>& M, int i, V ofe, V c, V e, V w, V n, V s) {
+    V acc = fma_(M.w[i][0], c, ofe);
     acc = fma_(M.w[i][1], e, acc);
     acc = fma_(M.w[i][2], w, acc);
     acc = fma_(M.w[i][3], n, acc);

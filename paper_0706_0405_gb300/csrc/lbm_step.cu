@@ -74,8 +74,13 @@ constexpr int kBoxFloats = kBoxX * kBoxY * 9;
 constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages start on 128-byte boundaries
 constexpr size_t kTileSmem = 128 + sizeof(float) * 2 * kStageFloats + 2 * sizeof(uint64_t);
 
+// Resident CTAs per SM the register budget is set for (3: 80 registers).
+#ifndef LBM_TILE_MIN_BLOCKS
+#define LBM_TILE_MIN_BLOCKS 3
+#endif
+
 template <int TM>
-__global__ void __launch_bounds__(kTileThreads, 3)
+__global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
     k_step_tile(const __grid_constant__ CUtensorMap tmap, float* __restrict__ fout, const Model<float> M,
                 const Grid<float> G, long long level, unsigned* status, int tiles_x, int ntiles) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -110,21 +115,21 @@ __global__ void __launch_bounds__(kTileThreads, 3)
     for (int k = 0;; ++k) {
         const int t = blockIdx.x + k * gridDim.x;
         if (t >= ntiles) break;
-        __syncthreads();  // every thread is done with the stage of tile k - 1
+        // one thread waits for tile k (the others sleep in the barrier rather
+        // than spin); the barrier then also says every thread is done with
+        // tile k - 1, whose stage the next copy overwrites
+        if (tid == 0 && !wait(k)) abort_flag = 1;
+        __syncthreads();
         if (abort_flag) {
             for (int j = waited + 1; j <= issued; ++j) wait(j);
             if (tid == 0) atomicOr(status, ST_TIMEOUT);
             return;
         }
+        waited = k;
         if (t + (int)gridDim.x < ntiles) {
             if (tid == 0) issue(t + gridDim.x, (k + 1) & 1);
             issued = k + 1;
         }
-        if (!wait(k)) {
-            abort_flag = 1;
-            continue;
-        }
-        waited = k;
         const int ix0 = (t % tiles_x) * kTileX + 2 * tx, iy = (t / tiles_x) * kTileY + ty;
         if (ix0 >= G.nx || iy >= G.ny) continue;
         const int nvalid = min(2, G.nx - ix0);
@@ -175,12 +180,6 @@ __global__ void __launch_bounds__(kTileThreads, 3)
                 write_ghosts(G, fout, ix, iy, v, level + 1);
             }
         }
-    }
-    __syncthreads();
-    if (abort_flag) {  // a wait of the last tile gave up
-        for (int j = waited + 1; j <= issued; ++j) wait(j);
-        if (tid == 0) atomicOr(status, ST_TIMEOUT);
-        return;
     }
     report(status, bits);
 }
