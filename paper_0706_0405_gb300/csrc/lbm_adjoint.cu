@@ -5,6 +5,7 @@
 // (Eqs. e16-e18) and of the moments (Eqs. e4, e5, e7).
 #include "lbm_launch.h"
 #include "lbm_linear.cuh"
+#include "lbm_ptx.cuh"
 
 namespace lbm {
 
@@ -18,12 +19,101 @@ __device__ __forceinline__ int kind_at(const Grid<S>& G, int side, int along_ind
     return side_part(G, side, along_index, level) ? G.kind_hi[side] : G.kind_lo[side];
 }
 
-// One adjoint step from level n + 1 back to level n (gather form over the
-// transposed star).  a: adjoint of level n + 1, abar: adjoint of level n
-// (interior of the padded layout; ghost cells are never read or written).
-// taup[block] += sum over the block's nodes of sum_i a_i (f^eq_i - f_i)
-// (per node in the storage precision, across nodes in FP64; the tau
-// derivative is -(dt / tau^2) times the total).
+// Adjoint of one node (gather form over the transposed star): from f at the
+// node (fv), the adjoint of level n + 1 at the node (av) and at its four star
+// neighbours (aL, aR, aD, aU; zero where the star leaves the grid through a
+// non-periodic side), the adjoint of level n at the node (o) before the ghost
+// links, and the node's tau term tn = sum_i a_i (f^eq_i - f_i).  Both adjoint
+// kernels use it, so they round alike.
+template <typename S, int TM>
+__device__ __forceinline__ void adjoint_core(const Model<S>& M, const S (&fv)[9], const S (&av)[9],
+                                             const S (&aL)[9], const S (&aR)[9], const S (&aD)[9],
+                                             const S (&aU)[9], S (&o)[9], S& tn) {
+    S rho, ux, uy, T;
+    moments<S, TM>(fv, M, rho, ux, uy, T);
+    S fe[9];
+    equilibrium(M, rho, ux, uy, T, fe);
+    tn = S(0);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) tn = fma_(av[i], sub_(fe[i], fv[i]), tn);
+    S h[4], g[9];
+    feq_vjp(M, rho, ux, uy, T, av, h);
+    moments_vjp(M, rho, ux, uy, T, h, g);
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        S r = fma_(M.w[j][0], av[j], mul_(M.omega, g[j]));
+        r = fma_(M.w[j][1], aL[j], r);  // the node left of me reads me as E
+        r = fma_(M.w[j][2], aR[j], r);  // the node right of me reads me as W
+        r = fma_(M.w[j][3], aD[j], r);  // the node below reads me as N
+        o[j] = fma_(M.w[j][4], aU[j], r);  // the node above reads me as S
+    }
+}
+
+// Ghost links of an edge node: its own ghost cell on a non-periodic side is
+// made from it (outflow: copied; reflect: mirrored), so the weight that read
+// that ghost comes back to it.  Dirichlet ghosts depend on nothing.
+template <typename S>
+__device__ __forceinline__ void adjoint_ghost_links(const Model<S>& M, const Grid<S>& G, long long level,
+                                                    int ix, int iy, const S (&av)[9], S (&o)[9]) {
+    const int kl = ix == 0 ? kind_at(G, S_LEFT, iy, level) : -1;
+    const int kr = ix == G.nx - 1 ? kind_at(G, S_RIGHT, iy, level) : -1;
+    const int kb = iy == 0 ? kind_at(G, S_BOTTOM, ix, level) : -1;
+    const int kt = iy == G.ny - 1 ? kind_at(G, S_TOP, ix, level) : -1;
+#pragma unroll
+    for (int j = 0; j < 9; ++j) {
+        S r = o[j];
+        if (kl == BC_OUTFLOW) r = fma_(M.w[j][2], av[j], r);
+        if (kl == BC_REFLECT) r = fma_(M.w[mirror_x(j)][2], av[mirror_x(j)], r);
+        if (kr == BC_OUTFLOW) r = fma_(M.w[j][1], av[j], r);
+        if (kr == BC_REFLECT) r = fma_(M.w[mirror_x(j)][1], av[mirror_x(j)], r);
+        if (kb == BC_OUTFLOW) r = fma_(M.w[j][4], av[j], r);
+        if (kb == BC_REFLECT) r = fma_(M.w[mirror_y(j)][4], av[mirror_y(j)], r);
+        if (kt == BC_OUTFLOW) r = fma_(M.w[j][3], av[j], r);
+        if (kt == BC_REFLECT) r = fma_(M.w[mirror_y(j)][3], av[mirror_y(j)], r);
+        o[j] = r;
+    }
+}
+
+// Periodic ghost cells of an adjoint level (the tile adjoint reads the star
+// of every node from a box that includes the ghost layer; ghost cells of
+// non-periodic sides stay zero).  Written by the node whose value wraps.
+template <typename S>
+__device__ __forceinline__ void write_periodic_ghosts(const Grid<S>& G, S* __restrict__ a, int ix, int iy,
+                                                      const S (&v)[9]) {
+    const size_t pl = (size_t)G.plane;
+    if (G.kind_lo[S_LEFT] == BC_PERIODIC) {
+        if (ix == G.nx - 1)
+            for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(iy + 1) * G.pitch + (PADX - 1)] = v[i];
+        if (ix == 0)
+            for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(iy + 1) * G.pitch + (PADX + G.nx)] = v[i];
+    }
+    if (G.kind_lo[S_BOTTOM] == BC_PERIODIC) {
+        if (iy == G.ny - 1)
+            for (int i = 0; i < 9; ++i) a[i * pl + (size_t)ix + PADX] = v[i];
+        if (iy == 0)
+            for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(G.ny + 1) * G.pitch + ix + PADX] = v[i];
+    }
+}
+
+// Star neighbours of node (ix, iy) on the grid, with periodic wrap; -1 if
+// none (a non-periodic edge).
+template <typename S>
+__device__ __forceinline__ void star_neighbours(const Grid<S>& G, int ix, int iy, int& xl, int& xr, int& yd,
+                                                int& yu) {
+    const bool perx = G.kind_lo[S_LEFT] == BC_PERIODIC;
+    const bool pery = G.kind_lo[S_BOTTOM] == BC_PERIODIC;
+    xl = ix > 0 ? ix - 1 : (perx ? G.nx - 1 : -1);
+    xr = ix < G.nx - 1 ? ix + 1 : (perx ? 0 : -1);
+    yd = iy > 0 ? iy - 1 : (pery ? G.ny - 1 : -1);
+    yu = iy < G.ny - 1 ? iy + 1 : (pery ? 0 : -1);
+}
+
+// One adjoint step from level n + 1 back to level n, one thread per node.
+// a: adjoint of level n + 1, abar: adjoint of level n (interior of the
+// padded layout; ghost cells are never read or written).
+// taup[block] += sum over the block's nodes of the node tau terms (per node
+// in the storage precision, across nodes in FP64; the tau derivative is
+// -(dt / tau^2) times the total).
 template <typename S, int TM>
 __global__ void __launch_bounds__(kThreads) k_adjoint(const S* __restrict__ f, const S* __restrict__ a,
                                                       S* __restrict__ abar, const Model<S> M,
@@ -37,54 +127,23 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const S* __restrict__ f, c
         const int iy = (int)(q / G.nx), ix = (int)(q % G.nx);
         const size_t pl = (size_t)G.plane;
         const size_t c = cell(G, ix, iy);
-        S fv[9], av[9];
+        int xl, xr, yd, yu;
+        star_neighbours(G, ix, iy, xl, xr, yd, yu);
+        S fv[9], av[9], aL[9], aR[9], aD[9], aU[9], o[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             fv[i] = f[i * pl + c];
             av[i] = a[i * pl + c];
+            aL[i] = xl >= 0 ? a[i * pl + cell(G, xl, iy)] : S(0);
+            aR[i] = xr >= 0 ? a[i * pl + cell(G, xr, iy)] : S(0);
+            aD[i] = yd >= 0 ? a[i * pl + cell(G, ix, yd)] : S(0);
+            aU[i] = yu >= 0 ? a[i * pl + cell(G, ix, yu)] : S(0);
         }
-        S rho, ux, uy, T;
-        moments<S, TM>(fv, M, rho, ux, uy, T);
-        S fe[9];
-        equilibrium(M, rho, ux, uy, T, fe);
-        // sum_i a_i (f^eq_i - f_i) in the storage precision per node; the
-        // sum over nodes is FP64
-        S tn = S(0);
+        adjoint_core<S, TM>(M, fv, av, aL, aR, aD, aU, o, tsum);
+        if (ix == 0 || iy == 0 || ix == G.nx - 1 || iy == G.ny - 1)
+            adjoint_ghost_links(M, G, level, ix, iy, av, o);
 #pragma unroll
-        for (int i = 0; i < 9; ++i) tn += av[i] * (fe[i] - fv[i]);
-        tsum = tn;
-        S h[4], g[9];
-        feq_vjp(M, rho, ux, uy, T, av, h);
-        moments_vjp(M, rho, ux, uy, T, h, g);
-        // neighbour sources of the transposed star, with periodic wrap
-        const bool perx = G.kind_lo[S_LEFT] == BC_PERIODIC;
-        const bool pery = G.kind_lo[S_BOTTOM] == BC_PERIODIC;
-        const int xl = ix > 0 ? ix - 1 : (perx ? G.nx - 1 : -1);
-        const int xr = ix < G.nx - 1 ? ix + 1 : (perx ? 0 : -1);
-        const int yd = iy > 0 ? iy - 1 : (pery ? G.ny - 1 : -1);
-        const int yu = iy < G.ny - 1 ? iy + 1 : (pery ? 0 : -1);
-        const int kl = ix == 0 ? kind_at(G, S_LEFT, iy, level) : -1;
-        const int kr = ix == G.nx - 1 ? kind_at(G, S_RIGHT, iy, level) : -1;
-        const int kb = iy == 0 ? kind_at(G, S_BOTTOM, ix, level) : -1;
-        const int kt = iy == G.ny - 1 ? kind_at(G, S_TOP, ix, level) : -1;
-#pragma unroll
-        for (int j = 0; j < 9; ++j) {
-            S o = M.w[j][0] * av[j] + M.omega * g[j];
-            if (xl >= 0) o += M.w[j][1] * a[j * pl + cell(G, xl, iy)];  // node left of me reads me as E
-            if (xr >= 0) o += M.w[j][2] * a[j * pl + cell(G, xr, iy)];  // node right of me reads me as W
-            if (yd >= 0) o += M.w[j][3] * a[j * pl + cell(G, ix, yd)];  // node below reads me as N
-            if (yu >= 0) o += M.w[j][4] * a[j * pl + cell(G, ix, yu)];  // node above reads me as S
-            // ghost links: my own ghost on a non-periodic side is made from me
-            if (kl == BC_OUTFLOW) o += M.w[j][2] * av[j];
-            if (kl == BC_REFLECT) o += M.w[mirror_x(j)][2] * av[mirror_x(j)];
-            if (kr == BC_OUTFLOW) o += M.w[j][1] * av[j];
-            if (kr == BC_REFLECT) o += M.w[mirror_x(j)][1] * av[mirror_x(j)];
-            if (kb == BC_OUTFLOW) o += M.w[j][4] * av[j];
-            if (kb == BC_REFLECT) o += M.w[mirror_y(j)][4] * av[mirror_y(j)];
-            if (kt == BC_OUTFLOW) o += M.w[j][3] * av[j];
-            if (kt == BC_REFLECT) o += M.w[mirror_y(j)][3] * av[mirror_y(j)];
-            abar[j * pl + c] = o;
-        }
+        for (int j = 0; j < 9; ++j) abar[j * pl + c] = o[j];
     }
     // warp sums in the storage precision (fixed shuffle tree), then the
     // block's eight warp sums in FP64 in a fixed order
@@ -96,6 +155,135 @@ __global__ void __launch_bounds__(kThreads) k_adjoint(const S* __restrict__ f, c
         double t = 0.0;
         for (int w = 0; w < kThreads / 32; ++w) t += sh[w];
         taup[blockIdx.x] += t;
+    }
+}
+
+// Periodic ghost cells of an adjoint level written by something other than
+// an adjoint kernel (the caller's adjoint, unpacked).
+__global__ void k_adjoint_wrap(float* __restrict__ a, const Grid<float> G) {
+    const long long n = (long long)G.nx * G.ny;
+    const long long q = blockIdx.x * (long long)kThreads + threadIdx.x;
+    if (q >= n) return;
+    const int iy = (int)(q / G.nx), ix = (int)(q % G.nx);
+    if (!(ix == 0 || iy == 0 || ix == G.nx - 1 || iy == G.ny - 1)) return;
+    float v[9];
+    const size_t c = cell(G, ix, iy);
+#pragma unroll
+    for (int i = 0; i < 9; ++i) v[i] = a[i * (size_t)G.plane + c];
+    write_periodic_ghosts(G, a, ix, iy, v);
+}
+
+// ------------------------------------------------------ FP32 tile adjoint
+// Persistent CTAs of 64 x 4 threads walk 64 x 4-node tiles, one node per
+// thread.  Per tile one thread issues two tiled tensor copies into one of two
+// shared-memory stages, completing on the stage's mbarrier: the adjoint of
+// level n + 1 over the tile and its halo (72 x 6 x 9; 4 extra columns each
+// side keep the x coordinate 16-byte aligned) and f of level n over the tile
+// (64 x 4 x 9).  Star neighbours come from shared memory; across a periodic
+// edge they come from the level's ghost cells, which the kernel that wrote
+// the level filled (write_periodic_ghosts).  One thread waits (bounded; on
+// give-up the CTA raises ST_TIMEOUT, drains its copies and returns) while the
+// others sleep in the barrier, which also frees the previous stage.
+constexpr int kAdjTX = 64, kAdjTY = 4, kAdjThreads = kAdjTX * kAdjTY;
+constexpr int kAdjBoxX = kAdjTX + 8, kAdjBoxY = kAdjTY + 2;
+constexpr int kAdjAFloats = kAdjBoxX * kAdjBoxY * 9;
+constexpr int kAdjAPad = (kAdjAFloats + 31) / 32 * 32;  // the f box starts on a 128-byte boundary
+constexpr int kAdjFFloats = kAdjTX * kAdjTY * 9;
+constexpr int kAdjStageFloats = (kAdjAPad + kAdjFFloats + 31) / 32 * 32;
+constexpr size_t kAdjSmem = 128 + sizeof(float) * 2 * kAdjStageFloats + 2 * sizeof(uint64_t);
+constexpr uint32_t kAdjWaitLimit = 1u << 22;
+
+template <int TM>
+__global__ void __launch_bounds__(kAdjThreads, 3)
+    k_adjoint_tile(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapF,
+                   float* __restrict__ abar, const Model<float> M,
+                   const Grid<float> G, long long level, double* __restrict__ taup, int tiles_x, int ntiles,
+                   unsigned* status) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    float* stage0 = reinterpret_cast<float*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(float) * 2 * kAdjStageFloats);
+    __shared__ int abort_flag;
+    __shared__ double wsum_sh[kAdjThreads / 32];
+    const int tid = threadIdx.x, tx = tid % kAdjTX, ty = tid / kAdjTX;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int tile, int st) {
+        const int x0 = (tile % tiles_x) * kAdjTX, y0 = (tile / tiles_x) * kAdjTY;
+        float* dst = stage0 + st * kAdjStageFloats;
+        mbar_arrive_expect_tx(&bar[st], (uint32_t)(sizeof(float) * (kAdjAFloats + kAdjFFloats)));
+        // adjoint box: array column x0 = interior x0 - 4, array row y0 = interior y0 - 1
+        tma_load_3d(dst, &tmapA, x0, y0, 0, &bar[st]);
+        // f box: the tile itself (array column x0 + 4, row y0 + 1)
+        tma_load_3d(dst + kAdjAPad, &tmapF, x0 + PADX, y0 + 1, 0, &bar[st]);
+    };
+    auto wait = [&](int k) { return mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), kAdjWaitLimit); };
+    int issued = -1, waited = -1;
+    if (blockIdx.x < ntiles) {
+        if (tid == 0) issue(blockIdx.x, 0);
+        issued = 0;
+    }
+    const size_t pl = (size_t)G.plane;
+    constexpr int PA = kAdjBoxX * kAdjBoxY, PF = kAdjTX * kAdjTY;
+    float wsum = 0.0f;  // this warp's tau terms, tile by tile in a fixed order (FP32 over a few tiles)
+    for (int k = 0;; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        if (tid == 0 && !wait(k)) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) {
+            for (int j = waited + 1; j <= issued; ++j) wait(j);
+            if (tid == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
+        waited = k;
+        if (t + (int)gridDim.x < ntiles) {
+            if (tid == 0) issue(t + gridDim.x, (k + 1) & 1);
+            issued = k + 1;
+        }
+        const int ix = (t % tiles_x) * kAdjTX + tx, iy = (t / tiles_x) * kAdjTY + ty;
+        float tn = 0.0f;
+        if (ix < G.nx && iy < G.ny) {
+            const float* sA = stage0 + (k & 1) * kAdjStageFloats + (ty + 1) * kAdjBoxX + (tx + 4);
+            const float* sF = stage0 + (k & 1) * kAdjStageFloats + kAdjAPad + ty * kAdjTX + tx;
+            // the box holds the star of every node: interior neighbours, the
+            // wrapped values in the ghost cells of periodic sides, zeros in
+            // the ghost cells of the others
+            float fv[9], av[9], aL[9], aR[9], aD[9], aU[9], o[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                const float* pA = sA + i * PA;
+                fv[i] = sF[i * PF];
+                av[i] = pA[0];
+                aL[i] = pA[-1];
+                aR[i] = pA[1];
+                aD[i] = pA[-kAdjBoxX];
+                aU[i] = pA[kAdjBoxX];
+            }
+            adjoint_core<float, TM>(M, fv, av, aL, aR, aD, aU, o, tn);
+            const size_t c = cell(G, ix, iy);
+            if (ix == 0 || iy == 0 || ix == G.nx - 1 || iy == G.ny - 1) {
+                adjoint_ghost_links(M, G, level, ix, iy, av, o);
+                write_periodic_ghosts(G, abar, ix, iy, o);
+            }
+#pragma unroll
+            for (int j = 0; j < 9; ++j) abar[j * pl + c] = o[j];
+        }
+#pragma unroll
+        for (int s = 16; s > 0; s >>= 1) tn += __shfl_down_sync(0xffffffffu, tn, s);
+        wsum += tn;  // lane 0 holds the warp's sum
+    }
+    if ((tid & 31) == 0) wsum_sh[tid / 32] = (double)wsum;
+    __syncthreads();
+    if (tid == 0) {
+        double tot = 0.0;
+        for (int w = 0; w < kAdjThreads / 32; ++w) tot += wsum_sh[w];
+        taup[blockIdx.x] += tot;
     }
 }
 
@@ -152,9 +340,49 @@ cudaError_t launch_adjoint(const S* f, const S* a, S* abar, const Model<S>& M, c
     return cudaGetLastError();
 }
 
+template <int TM>
+cudaError_t launch_adjoint_tile(const CUtensorMap& tmapA, const CUtensorMap& tmapF, float* abar,
+                                const Model<float>& M, const Grid<float>& G, long long level, double* taup,
+                                unsigned* status, cudaStream_t st) {
+    auto kern = k_adjoint_tile<TM>;
+    cudaError_t e = allow_smem<k_adjoint_tile<TM>>(kAdjSmem);
+    if (e != cudaSuccess) return e;
+    const int tiles_x = (G.nx + kAdjTX - 1) / kAdjTX;
+    const int ntiles = tiles_x * ((G.ny + kAdjTY - 1) / kAdjTY);
+    static int full_wave = 0;
+    if (full_wave == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjThreads, kAdjSmem);
+        full_wave = sms * (per_sm > 0 ? per_sm : 1);
+    }
+    const int grid = ntiles < full_wave ? ntiles : full_wave;
+    kern<<<grid, kAdjThreads, kAdjSmem, st>>>(tmapA, tmapF, abar, M, G, level, taup, tiles_x, ntiles, status);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adjoint_wrap(float* a, const Grid<float>& G, cudaStream_t st) {
+    if (G.kind_lo[S_LEFT] != BC_PERIODIC && G.kind_lo[S_BOTTOM] != BC_PERIODIC) return cudaSuccess;
+    k_adjoint_wrap<<<blocks_for((long long)G.nx * G.ny, kThreads), kThreads, 0, st>>>(a, G);
+    return cudaGetLastError();
+}
+
+void adjoint_tile_boxes(int* ax, int* ay, int* fx, int* fy) {
+    *ax = kAdjBoxX;
+    *ay = kAdjBoxY;
+    *fx = kAdjTX;
+    *fy = kAdjTY;
+}
+
+// Slots of the tau partials: one per block of the thread-per-node kernel,
+// and at least one per CTA of the tile kernel (whose grid never exceeds its
+// tile count).
 template <typename S>
 int adjoint_partials(const Grid<S>& G) {
-    return (int)blocks_for((long long)G.nx * G.ny, kThreads);
+    const int simple = (int)blocks_for((long long)G.nx * G.ny, kThreads);
+    const int tiles = ((G.nx + kAdjTX - 1) / kAdjTX) * ((G.ny + kAdjTY - 1) / kAdjTY);
+    return simple > tiles ? simple : tiles;
 }
 
 template <typename S, int TM>
@@ -186,6 +414,18 @@ LBM_ADJ_INST(float, T_INT64)
 LBM_ADJ_INST(float, T_DF)
 LBM_ADJ_INST(float, T_CONS)
 #undef LBM_ADJ_INST
+template cudaError_t launch_adjoint_tile<T_INT32>(const CUtensorMap&, const CUtensorMap&, float*,
+                                                  const Model<float>&, const Grid<float>&, long long, double*,
+                                                  unsigned*, cudaStream_t);
+template cudaError_t launch_adjoint_tile<T_INT64>(const CUtensorMap&, const CUtensorMap&, float*,
+                                                  const Model<float>&, const Grid<float>&, long long, double*,
+                                                  unsigned*, cudaStream_t);
+template cudaError_t launch_adjoint_tile<T_DF>(const CUtensorMap&, const CUtensorMap&, float*,
+                                               const Model<float>&, const Grid<float>&, long long, double*,
+                                               unsigned*, cudaStream_t);
+template cudaError_t launch_adjoint_tile<T_CONS>(const CUtensorMap&, const CUtensorMap&, float*,
+                                                 const Model<float>&, const Grid<float>&, long long, double*,
+                                                 unsigned*, cudaStream_t);
 template int adjoint_partials<double>(const Grid<double>&);
 template int adjoint_partials<float>(const Grid<float>&);
 template cudaError_t launch_feq_vjp<double>(const double*, const double*, const double*, const double*,

@@ -50,6 +50,11 @@ struct lbm_ctx {
     std::vector<void*> ck;       // ck[k] holds level ck_base + k * ck_every (padded, with ghosts)
     std::vector<void*> seg;      // recomputed levels of one segment
     void* adj[2] = {nullptr, nullptr};
+    // FP32 tile adjoint: tensor maps of the adjoint levels and, per segment
+    // level, of its tile (adjoint) and of its halo box (tile recomputation)
+    CUtensorMap adj_tmap[2];
+    std::vector<CUtensorMap> seg_tmapF, seg_tmapS;
+    bool adj_tmaps_ok = false;
     double* d_taup = nullptr;
     double* h_taup = nullptr;
     int ntaup = 0;
@@ -113,6 +118,7 @@ Model<double> build_model(double b, double tau, double dt, double dx, const lbm_
     M.c2s = c2s;
     M.eta2 = e0s;
     M.inv_b = 1.0 / b;
+    M.b = b;
     M.k0 = (b - 2.0) / e0s;
     const double q1 = 4.0 * (c1s - c2s), q5 = 4.0 * (c2s - c1s);
     M.a1c = -c2s / q1;
@@ -390,12 +396,11 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 3D map (x: pitch columns, y: ny + 2 rows, z: 9 planes) of one FP32 level.
-bool make_tmap(CUtensorMap* m, void* base, const lbm_ctx& c) {
+// 3D map (x: pitch columns, y: ny + 2 rows, z: 9 planes) of one FP32 level
+// with a bx x by x 9 box.
+bool make_tmap_box(CUtensorMap* m, void* base, const lbm_ctx& c, int bx, int by) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
-    int bx = 0, by = 0;
-    tile_box_dims(&bx, &by);
     const cuuint64_t dims[3] = {(cuuint64_t)c.pitch, (cuuint64_t)(c.ny + 2), 9};
     const cuuint64_t strides[2] = {(cuuint64_t)c.pitch * 4, (cuuint64_t)c.plane * 4};
     const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 9};
@@ -403,6 +408,13 @@ bool make_tmap(CUtensorMap* m, void* base, const lbm_ctx& c) {
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// The step kernel's map (tile_box_dims box).
+bool make_tmap(CUtensorMap* m, void* base, const lbm_ctx& c) {
+    int bx = 0, by = 0;
+    tile_box_dims(&bx, &by);
+    return make_tmap_box(m, base, c, bx, by);
 }
 
 struct CkptHeader {
@@ -724,16 +736,29 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, int n, void* abar, double* dL_dtau) {
                     c->step - c->ck_base);
     if (n == 0) return LBM_OK;
     const size_t fb = nodes(c) * c->esize, lb = level_bytes(c);
+    const bool fp32 = c->prec != LBM_FP64;
+    int abx = 0, aby = 0, afx = 0, afy = 0;
+    adjoint_tile_boxes(&abx, &aby, &afx, &afy);
     for (int k = 0; k < 2; ++k)
         if (!c->adj[k]) {
             LBM_CUDA(c, cudaMalloc(&c->adj[k], lb), "allocating adjoint levels");
             LBM_CUDA(c, cudaMemsetAsync(c->adj[k], 0, lb, c->stream), "clearing adjoint levels");
+            if (k == 1)
+                c->adj_tmaps_ok = fp32 && make_tmap_box(&c->adj_tmap[0], c->adj[0], *c, abx, aby) &&
+                                  make_tmap_box(&c->adj_tmap[1], c->adj[1], *c, abx, aby);
         }
     while ((int)c->seg.size() < c->ck_every) {
         void* p = nullptr;
         LBM_CUDA(c, cudaMalloc(&p, lb), "allocating segment levels");
         c->seg.push_back(p);
+        CUtensorMap mf{}, ms{};
+        if (c->adj_tmaps_ok && !(make_tmap_box(&mf, p, *c, afx, afy) && make_tmap(&ms, p, *c)))
+            c->adj_tmaps_ok = false;
+        c->seg_tmapF.push_back(mf);
+        c->seg_tmapS.push_back(ms);
     }
+    // the tile adjoint (and tile recomputation) with the tile step kernel
+    const bool tile = c->adj_tmaps_ok && c->cfg.variant == STEP_TILE;
     const int np = c->prec == LBM_FP64 ? adjoint_partials(c->gd) : adjoint_partials(c->gf);
     if (c->ntaup < np) {
         cudaFree(c->d_taup);
@@ -756,9 +781,10 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, int n, void* abar, double* dL_dtau) {
         using S = decltype(tag);
         return launch_unpack<S>(static_cast<S*>(c->adj[0]), (const S*)dense_in, grid_of<S>(c), c->stream);
     });
+    if (e == cudaSuccess && tile) e = launch_adjoint_wrap(static_cast<float*>(c->adj[0]), c->gf, c->stream);
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_adjoint_step: unpacking abar");
-    StepConfig rcfg = c->cfg;  // recomputation writes segment buffers, which have no tensor maps
-    if (rcfg.variant == STEP_TILE) rcfg = StepConfig{STEP_SIMPLE, 0, 0, 0};
+    StepConfig rcfg = c->cfg;  // recomputation reads segment buffers through their own tensor maps
+    if (rcfg.variant == STEP_TILE && !tile) rcfg = StepConfig{STEP_SIMPLE, 0, 0, 0};
     int ac = 0;
     long long L = c->step;
     const long long target = c->step - n;
@@ -770,6 +796,7 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, int n, void* abar, double* dL_dtau) {
         LBM_CUDA(c, cudaMemcpyAsync(c->seg[0], c->ck[(size_t)k], lb, cudaMemcpyDeviceToDevice, c->stream),
                  "restoring a checkpoint");
         for (long long l = c0; l < L - 1; ++l) {
+            if (tile) rcfg.tmap = &c->seg_tmapS[(size_t)(l - c0)];
             e = dispatch(c, [&](auto tag, auto tm) {
                 using S = decltype(tag);
                 constexpr int TM = decltype(tm)::value;
@@ -783,6 +810,12 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, int n, void* abar, double* dL_dtau) {
             e = dispatch(c, [&](auto tag, auto tm) {
                 using S = decltype(tag);
                 constexpr int TM = decltype(tm)::value;
+                if constexpr (std::is_same<S, float>::value) {
+                    if (tile)
+                        return launch_adjoint_tile<TM>(c->adj_tmap[ac], c->seg_tmapF[(size_t)(l - c0)],
+                                                       static_cast<float*>(c->adj[ac ^ 1]), model_of<S>(c),
+                                                       grid_of<S>(c), l, c->d_taup, c->d_status, c->stream);
+                }
                 return launch_adjoint<S, TM>(static_cast<const S*>(c->seg[(size_t)(l - c0)]),
                                              static_cast<const S*>(c->adj[ac]), static_cast<S*>(c->adj[ac ^ 1]),
                                              model_of<S>(c), grid_of<S>(c), l, c->d_taup, c->stream);

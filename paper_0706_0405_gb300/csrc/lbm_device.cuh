@@ -48,6 +48,7 @@ struct Model {
     S c1, d;          // axis speed c1; diagonal component c2 / sqrt(2)
     S c1s, c2s, eta2; // c1^2, c2^2, eta0^2
     S inv_b;          // 1 / b
+    S b;              // b = 2 / (gamma - 1)
     S k0;             // A_0 / T = (b - 2) / eta0^2 (Eq. e17)
     S a1c, a1T, a1u;  // A_1..4 = a1c + a1T T + a1u u^2 (Eq. e17)
     S a5c, a5T, a5u;  // A_5..8

@@ -8,6 +8,21 @@
 
 namespace lbm {
 
+// Raise a kernel's dynamic shared-memory limit once per device (the setting
+// persists; calling the runtime for it on every launch costs microseconds
+// per step on small grids).
+template <auto Kern>
+inline cudaError_t allow_smem(size_t bytes) {
+    static unsigned done = 0;  // per kernel: one bit per device ordinal < 32
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned bit = dev < 32 ? 1u << dev : 0u;
+    if (bit && (done & bit)) return cudaSuccess;
+    const cudaError_t e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+    if (e == cudaSuccess) done |= bit;
+    return e;
+}
+
 // Kernel variant and launch shape of the step (chosen by the host, see
 // lbm_tune in lbm.h).
 enum StepVariant : int { STEP_SIMPLE = 0, STEP_RING = 1, STEP_VEC = 2, STEP_TILE = 3 };
@@ -62,6 +77,19 @@ cudaError_t launch_adjoint(const S* f, const S* a, S* abar, const Model<S>& M, c
                            long long level, double* taup, cudaStream_t st);
 template <typename S>
 int adjoint_partials(const Grid<S>& G);
+// FP32 tile adjoint: tmapA over the adjoint level n + 1 (box from
+// adjoint_tile_boxes: ax x ay x 9), whose periodic ghost cells must hold the
+// wrapped values and whose other ghost cells must be zero; tmapF over the
+// forward level n (box fx x fy x 9).  Writes abar's interior and periodic
+// ghost cells.
+template <int TM>
+cudaError_t launch_adjoint_tile(const CUtensorMap& tmapA, const CUtensorMap& tmapF, float* abar,
+                                const Model<float>& M, const Grid<float>& G, long long level, double* taup,
+                                unsigned* status, cudaStream_t st);
+// Periodic ghost cells of an adjoint level from its interior (no-op without
+// periodic sides).
+cudaError_t launch_adjoint_wrap(float* a, const Grid<float>& G, cudaStream_t st);
+void adjoint_tile_boxes(int* ax, int* ay, int* fx, int* fy);
 // Seed abar (dense 9 x n) = sum_m qbar_m dq_m/df at the level f; null qbar = 0.
 template <typename S, int TM>
 cudaError_t launch_moments_vjp(const S* f, const S* qr, const S* qx, const S* qy, const S* qT, S* abar,

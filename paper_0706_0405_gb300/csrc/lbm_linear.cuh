@@ -10,54 +10,62 @@
 namespace lbm {
 
 // Partial derivatives of f^eq_i with respect to (rho, ux, uy, T), contracted
-// with an adjoint vector a: h = sum_i a_i dF_i/dq.
+// with an adjoint vector a: h = sum_i a_i dF_i/dq.  With
+// F_i = rho (A + B s_i + D s_i^2), s_i = v_i.u, and A, B depending on T and
+// u^2 (Eqs. e16-e18), the sums over each velocity set reduce to sums and
+// differences of the opposite pairs: on the axes s = -p, -q, p, q for
+// i = 1..4 (p = c1 ux, q = c1 uy); on the diagonals s = -r, m, r, -m for
+// i = 5..8 (r = d (ux + uy), m = d (ux - uy), d = c2 / sqrt 2).
 template <typename S>
-__host__ __device__ __forceinline__ void feq_vjp(const Model<S>& M, S rho, S ux, S uy, S T, const S (&a)[9],
-                                        S (&h)[4]) {
+__device__ __forceinline__ void feq_vjp(const Model<S>& M, S rho, S ux, S uy, S T, const S (&a)[9],
+                                                 S (&h)[4]) {
     const S u2 = ux * ux + uy * uy;
     const S A1 = M.a1c + M.a1T * T + M.a1u * u2, A5 = M.a5c + M.a5T * T + M.a5u * u2;
     const S B1 = M.b1c + M.b1T * T + M.b1u * u2, B5 = M.b5c + M.b5T * T + M.b5u * u2;
-    const int sx[9] = {0, -1, 0, 1, 0, -1, 1, 1, -1};
-    const int sy[9] = {0, 0, -1, 0, 1, -1, -1, 1, 1};
-    S hr = a[0] * (M.k0 * T), hx = S(0), hy = S(0), hT = a[0] * (rho * M.k0);
-#pragma unroll
-    for (int i = 1; i < 9; ++i) {
-        const bool axis = i <= 4;
-        const S mag = axis ? M.c1 : M.d;
-        const S vx = sx[i] * mag, vy = sy[i] * mag;
-        const S A = axis ? A1 : A5, B = axis ? B1 : B5, D = axis ? M.D1 : M.D5;
-        const S Au = axis ? M.a1u : M.a5u, Bu = axis ? M.b1u : M.b5u;
-        const S AT = axis ? M.a1T : M.a5T, BT = axis ? M.b1T : M.b5T;
-        const S vu = vx * ux + vy * uy;
-        hr += a[i] * (A + B * vu + D * vu * vu);
-        const S g = S(2) * (Au + Bu * vu);   // d(A + B v.u)/d(u^2) * 2
-        const S k = B + S(2) * D * vu;        // d(B v.u + D (v.u)^2)/d(v.u)
-        hx += a[i] * rho * (g * ux + k * vx);
-        hy += a[i] * rho * (g * uy + k * vy);
-        hT += a[i] * rho * (AT + BT * vu);
-    }
-    h[0] = hr;
-    h[1] = hx;
-    h[2] = hy;
-    h[3] = hT;
+    const S p = M.c1 * ux, q = M.c1 * uy, r = M.d * (ux + uy), m = M.d * (ux - uy);
+    // pair sums (P) and differences (Q, the + direction minus the - one)
+    const S P13 = a[1] + a[3], Q13 = a[3] - a[1], P24 = a[2] + a[4], Q24 = a[4] - a[2];
+    const S P57 = a[5] + a[7], Q57 = a[7] - a[5], P68 = a[6] + a[8], Q68 = a[6] - a[8];
+    // per set: sum a, sum a s, sum a s^2
+    const S Sa1 = P13 + P24, Ss1 = Q13 * p + Q24 * q, Sss1 = P13 * p * p + P24 * q * q;
+    const S Sa5 = P57 + P68, Ss5 = Q57 * r + Q68 * m, Sss5 = P57 * r * r + P68 * m * m;
+    // sum a v_x, sum a v_y and sum a s v_x, sum a s v_y per set
+    const S Svx1 = M.c1 * Q13, Svy1 = M.c1 * Q24;
+    const S Ssvx1 = M.c1 * p * P13, Ssvy1 = M.c1 * q * P24;
+    const S Svx5 = M.d * (Q57 + Q68), Svy5 = M.d * (Q57 - Q68);
+    const S Ssvx5 = M.d * (r * P57 + m * P68), Ssvy5 = M.d * (r * P57 - m * P68);
+    h[0] = a[0] * (M.k0 * T) + (A1 * Sa1 + B1 * Ss1 + M.D1 * Sss1) + (A5 * Sa5 + B5 * Ss5 + M.D5 * Sss5);
+    // d/du: rho [2 (A_u + B_u s) u + (B + 2 D s) v] summed with a
+    const S G1 = S(2) * (M.a1u * Sa1 + M.b1u * Ss1), G5 = S(2) * (M.a5u * Sa5 + M.b5u * Ss5);
+    h[1] = rho * ((G1 + G5) * ux + B1 * Svx1 + S(2) * M.D1 * Ssvx1 + B5 * Svx5 + S(2) * M.D5 * Ssvx5);
+    h[2] = rho * ((G1 + G5) * uy + B1 * Svy1 + S(2) * M.D1 * Ssvy1 + B5 * Svy5 + S(2) * M.D5 * Ssvy5);
+    h[3] = rho * (a[0] * M.k0 + M.a1T * Sa1 + M.b1T * Ss1 + M.a5T * Sa5 + M.b5T * Ss5);
 }
 
 // g_j = sum_m h_m dq_m/df_j at moments (rho, ux, uy, T):
 // drho/df_j = 1, du/df_j = (v_j - u) / rho, dT/df_j = (|v_j - u|^2 + eta_j^2 - b T) / (b rho).
+// Expanding |v_j - u|^2 with H = (h_ux, h_uy) / rho and H3 = h_T / (b rho):
+// g_j = G0 + v_j.(X, Y) + H3 (|v_j|^2 + eta_j^2), where (X, Y) = H - 2 H3 u and
+// G0 = h_rho - H.u + H3 (u^2 - b T); each velocity set then needs one product
+// per direction.
 template <typename S>
-__host__ __device__ __forceinline__ void moments_vjp(const Model<S>& M, S rho, S ux, S uy, S T, const S (&h)[4],
+__device__ __forceinline__ void moments_vjp(const Model<S>& M, S rho, S ux, S uy, S T, const S (&h)[4],
                                             S (&g)[9]) {
-    const int sx[9] = {0, -1, 0, 1, 0, -1, 1, 1, -1};
-    const int sy[9] = {0, 0, -1, 0, 1, -1, -1, 1, 1};
-    const S ir = S(1) / rho;
-    const S b = S(1) / M.inv_b;
-#pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        const S mag = j == 0 ? S(0) : (j <= 4 ? M.c1 : M.d);
-        const S dx = sx[j] * mag - ux, dy = sy[j] * mag - uy;
-        const S e2 = j == 0 ? M.eta2 : S(0);
-        g[j] = h[0] + (h[1] * dx + h[2] * dy) * ir + h[3] * (dx * dx + dy * dy + e2 - b * T) * ir * M.inv_b;
-    }
+    const S ir = rcp_(rho);
+    const S H1 = h[1] * ir, H2 = h[2] * ir, H3 = h[3] * ir * M.inv_b;
+    const S G0 = h[0] - H1 * ux - H2 * uy + H3 * (ux * ux + uy * uy - M.b * T);
+    const S X = H1 - S(2) * H3 * ux, Y = H2 - S(2) * H3 * uy;
+    const S g1 = G0 + H3 * M.c1s, g5 = G0 + H3 * M.c2s;
+    const S cx = M.c1 * X, cy = M.c1 * Y, dp = M.d * (X + Y), dm = M.d * (X - Y);
+    g[0] = G0 + H3 * M.eta2;
+    g[1] = g1 - cx;
+    g[2] = g1 - cy;
+    g[3] = g1 + cx;
+    g[4] = g1 + cy;
+    g[5] = g5 - dp;
+    g[6] = g5 + dm;
+    g[7] = g5 + dp;
+    g[8] = g5 - dm;
 }
 
 }  // namespace lbm

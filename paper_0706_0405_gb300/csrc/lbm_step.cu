@@ -194,7 +194,7 @@ cudaError_t launch_tile(const CUtensorMap& tmap, float* fout, const Model<float>
                         long long level, unsigned* status, int grid_hint, cudaStream_t st) {
     constexpr size_t smem = kTileSmem;
     auto kern = k_step_tile<TM>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = allow_smem<k_step_tile<TM>>(smem);
     if (e != cudaSuccess) return e;
     const int tiles_x = (G.nx + kTileX - 1) / kTileX;
     const int ntiles = tiles_x * ((G.ny + kTileY - 1) / kTileY);
@@ -367,7 +367,7 @@ cudaError_t launch_ring(const float* fin, float* fout, const Model<float>& M, co
     constexpr size_t smem = ring_smem_bytes<TX, R>();
     auto kern = k_step_ring<TX, R, TM>;
     if (smem > 48 * 1024) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaError_t e = allow_smem<k_step_ring<TX, R, TM>>(smem);
         if (e != cudaSuccess) return e;
     }
     int grid = grid_hint;

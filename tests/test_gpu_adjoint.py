@@ -157,3 +157,37 @@ def test_adjoint_needs_a_recording():
         assert ei.value.status == lbm.LBM_E_INVAL
         lbm.lbm_adjoint_step(lat.ctx, 3, abar)  # host array, exactly what was recorded
         assert lat.step_count == 3
+
+
+@pytest.mark.parametrize("sides", [MIXED, (Side("periodic"),) * 4, (Side("reflect"),) * 4])
+def test_fp32_tile_adjoint_matches_oracle_and_simple_kernel(sides):
+    """One FP32 adjoint step on a 150 x 37 grid (tiles of 64 x 4 with ragged
+    edges, several CTAs) through the tile kernel (the default launch) and
+    through the thread-per-node kernel (launch variant 0): both equal the
+    FP64 oracle adjoint to FP32 accuracy, and each other to a few ulp."""
+    rng = np.random.Generator(np.random.PCG64(12))
+    p = W.uniform(150, 37, (1.0, 0.0, 0.0, 1.0), dx=0.1, alpha=0.2, sides=sides, lam_scale=2.0)
+    p = p.with_(tau=p.dt / 0.8)
+    f0 = _random_state(p, rng)
+    w = rng.standard_normal((9, p.ny, p.nx))
+    n = 5
+    out = {}
+    for variant in (3, 0):
+        with lbm.Lattice(p, "fp32_cons") as lat:
+            lbm.lbm_set_launch(lat.ctx, variant)
+            lat.set_f(f0.astype(np.float32), n)
+            lbm.lbm_record(lat.ctx, 1)
+            lat.step(1)
+            abar = w.astype(np.float32)
+            dtau = lbm.lbm_adjoint_step(lat.ctx, 1, abar)
+            out[variant] = (abar.astype(np.float64), dtau)
+    state = oracle.empty_state(p)
+    oracle.interior(state)[:] = f0.astype(np.float32).astype(np.float64)
+    want, want_tau = oracle.adjoint_step(p, state, n, np.pad(w.astype(np.float32).astype(np.float64),
+                                                              ((0, 0), (1, 1), (1, 1))))
+    wi = oracle.interior(want)
+    scale = np.max(np.abs(wi))
+    for variant, (abar, dtau) in out.items():
+        assert np.max(np.abs(abar - wi)) <= 2e-5 * scale, variant
+        assert dtau == pytest.approx(want_tau, rel=1e-4), variant
+    assert np.max(np.abs(out[3][0] - out[0][0])) <= 1e-6 * scale
