@@ -1159,11 +1159,18 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
             for (int x0 = 0; x0 < probs[p].nx; x0 += tw) tiles.push_back(make_int4(p, x0, y0, 0));
     b->ntiles = (int)tiles.size();
     std::vector<BatchProb> hp(nprob);
+    int bbx = 0, bby = 0;
+    batch_box_dims(&bbx, &bby);
     for (int p = 0; p < nprob; ++p) {
         hp[p].f[0] = static_cast<float*>(b->ctx[p]->f[0]);
         hp[p].f[1] = static_cast<float*>(b->ctx[p]->f[1]);
         hp[p].M = b->ctx[p]->mf;
         hp[p].G = b->ctx[p]->gf;
+        for (int k = 0; k < 2; ++k)
+            if (!make_tmap_box(&hp[p].tm[k], b->ctx[p]->f[k], *b->ctx[p], bbx, bby)) {
+                lbm_batch_destroy(b);
+                return bfail(nullptr, LBM_E_CUDA, "lbm_batch_create: tensor maps unavailable on this driver");
+            }
     }
     cudaError_t e = cudaMalloc((void**)&b->d_probs, sizeof(BatchProb) * nprob);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles, sizeof(int4) * tiles.size());

@@ -2,12 +2,13 @@
 // boundary kinds) advanced by one persistent cooperative launch: every CTA
 // walks a contiguous share of the (problem, 64 x 4 tile) list per step, and a
 // bounded grid barrier separates the steps.  Each tile and its halo (72 x 6
-// x 9 floats) are loaded into shared memory by all threads with 16-byte
-// reads through L2 (data of the previous step written by other CTAs), then
-// every thread updates one node with the same per-node arithmetic as the
-// single-grid kernels, so each problem's levels are bit-identical to stepping
-// it alone.
+// x 9 floats) arrive in shared memory by one tiled tensor copy through the
+// problem's own tensor map, double-buffered so that the next tile of the
+// CTA's share is in flight while the current one is computed; every thread
+// then updates one node with the same per-node arithmetic as the single-grid
+// kernels, so each problem's levels are bit-identical to stepping it alone.
 #include "lbm_launch.h"
+#include "lbm_ptx.cuh"
 
 namespace lbm {
 
@@ -16,11 +17,16 @@ constexpr int kBatchThreads = 256;
 constexpr int kTileW = 64;  // columns per tile (one node per thread)
 constexpr int kTileH = 4;   // rows per tile
 constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz, then give up
+constexpr uint32_t kBatchWaitLimit = 1u << 22;       // mbarrier probes before a wait gives up
 
 // Bounded grid-wide barrier for a cooperative launch.  Returns false (and
-// sets ST_TIMEOUT) if the barrier did not complete in time.
+// sets ST_TIMEOUT) if the barrier did not complete in time.  The stores of
+// the step are ordered before the async-proxy reads (tensor copies) of the
+// next step on both sides: every thread fences after its stores, and the
+// thread that issues the copies fences after the barrier.
 __device__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned* status) {
     __shared__ int ok;
+    fence_proxy_async_global();
     __syncthreads();
     if (threadIdx.x == 0) {
         ok = 1;
@@ -43,6 +49,7 @@ __device__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned* 
             }
         }
         __threadfence();
+        fence_proxy_async_global();
     }
     __syncthreads();
     return ok != 0;
@@ -56,6 +63,9 @@ __device__ __forceinline__ void copy_words(S* dst, const S* src, int n) {
 constexpr int kBoxW = kTileW + 8;  // 4 extra columns each side keep 16-byte alignment
 constexpr int kBoxH = kTileH + 2;
 constexpr int kBoxPlane = kBoxW * kBoxH;
+constexpr int kBoxFloats = 9 * kBoxPlane;
+constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages on 128-byte boundaries
+constexpr size_t kBatchSmem = 128 + sizeof(float) * 2 * kStageFloats + 2 * sizeof(uint64_t);
 
 template <int TM>
 __global__ void __launch_bounds__(kBatchThreads)
@@ -63,52 +73,73 @@ __global__ void __launch_bounds__(kBatchThreads)
             long long* level_ptr, unsigned* bar_count, unsigned* bar_gen, unsigned* status) {
     __shared__ Model<float> sM;
     __shared__ Grid<float> sG;
-    __shared__ __align__(16) float box[9 * kBoxPlane];
+    __shared__ int abort_flag;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    float* box0 = reinterpret_cast<float*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(float) * 2 * kStageFloats);
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
     const long long level0 = *(volatile long long*)level_ptr;
     unsigned bits = 0;
-    const int r = threadIdx.x / kTileW, cx = threadIdx.x % kTileW;
+    const int r = tid / kTileW, cx = tid % kTileW;
     // a contiguous run of tiles per CTA: consecutive tiles mostly share a
     // problem, so its constants are copied to shared memory rarely
     const int per = (ntiles + gridDim.x - 1) / gridDim.x;
     const int t0 = blockIdx.x * per, t1 = min(ntiles, t0 + per);
-    constexpr int kVecs = 9 * kBoxH * (kBoxW / 4);  // float4 loads per box
+    // running index k of this CTA's tiles over all steps: stage k & 1,
+    // phase parity (k >> 1) & 1
+    auto issue = [&](int t, int k, int par) {
+        const int4 T = tiles[t];
+        mbar_arrive_expect_tx(&bar[k & 1], (uint32_t)(sizeof(float) * kBoxFloats));
+        // array column T.y (interior column T.y - 4), array row T.z (interior row T.z - 1)
+        tma_load_3d(box0 + (k & 1) * kStageFloats, &probs[T.x].tm[par], T.y, T.z, 0, &bar[k & 1]);
+    };
+    auto wait = [&](int k) { return mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), kBatchWaitLimit); };
+    int k = 0, issued = -1, waited = -1;
     for (int s = 0; s < nsteps; ++s) {
         const long long level = level0 + s;
         const int par = (int)(level & 1);
         if (*(volatile unsigned*)status & ST_TIMEOUT) return;
+        if (t0 < t1) {
+            if (tid == 0) issue(t0, k, par);
+            issued = k;
+        }
         int cur = -1;
-        for (int t = t0; t < t1; ++t) {
+        for (int t = t0; t < t1; ++t, ++k) {
+            // one thread waits for tile k; the barrier also says every thread
+            // is done with tile k - 1 (its box and the problem constants)
+            if (tid == 0 && !wait(k)) abort_flag = 1;
+            __syncthreads();
+            if (abort_flag) {
+                for (int j = waited + 1; j <= issued; ++j) wait(j);
+                if (tid == 0) atomicOr(status, ST_TIMEOUT);
+                return;
+            }
+            waited = k;
+            if (t + 1 < t1) {
+                if (tid == 0) issue(t + 1, k + 1, par);
+                issued = k + 1;
+            }
             const int4 T = tiles[t];
             const BatchProb& P = probs[T.x];
-            __syncthreads();  // previous tile's box (and constants) no longer read
             if (T.x != cur) {
                 copy_words(reinterpret_cast<float*>(&sM), reinterpret_cast<const float*>(&P.M),
                            (int)(sizeof(Model<float>) / sizeof(float)));
                 copy_words(reinterpret_cast<int*>(&sG), reinterpret_cast<const int*>(&P.G),
                            (int)(sizeof(Grid<float>) / sizeof(int)));
                 cur = T.x;
+                __syncthreads();
             }
-            // box: array rows T.z .. T.z + kBoxH - 1 (interior rows T.z - 1 ..),
-            // array columns T.y .. T.y + kBoxW - 1 (interior columns T.y - 4 ..);
-            // whole float4 groups inside the row pitch only (the columns any
-            // node reads always are), read through L2
-            const float* fin = P.f[par];
-            const int pitch = P.G.pitch, rows = P.G.ny + 2;
-            const size_t pl = (size_t)P.G.plane;
-            for (int v = threadIdx.x; v < kVecs; v += kBatchThreads) {
-                const int i = v / (kBoxH * (kBoxW / 4));
-                const int rem = v % (kBoxH * (kBoxW / 4));
-                const int yy = rem / (kBoxW / 4), xx = (rem % (kBoxW / 4)) * 4;
-                const int ay = T.z + yy, ax = T.y + xx;
-                if (ay < rows && ax + 4 <= pitch) {
-                    const float4 q = __ldcg(reinterpret_cast<const float4*>(fin + i * pl + (size_t)ay * pitch + ax));
-                    *reinterpret_cast<float4*>(&box[i * kBoxPlane + yy * kBoxW + xx]) = q;
-                }
-            }
-            __syncthreads();
             const int ix = T.y + cx, iy = T.z + r;
             if (ix < sG.nx && iy < sG.ny) {
-                const float* b = box + (r + 1) * kBoxW + (cx + 4);
+                const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxW + (cx + 4);
                 float f[9];
 #pragma unroll
                 for (int i = 0; i < 9; ++i) f[i] = b[i * kBoxPlane];
@@ -123,6 +154,7 @@ __global__ void __launch_bounds__(kBatchThreads)
                     o[i] = update(sM, i, ofe[i], f[i], bp[1], bp[-1], bp[kBoxW], bp[-kBoxW]);
                 }
                 float* fout = P.f[par ^ 1];
+                const size_t pl = (size_t)sG.plane;
                 const size_t c = cell(sG, ix, iy);
 #pragma unroll
                 for (int i = 0; i < 9; ++i) fout[i * pl + c] = o[i];
@@ -143,16 +175,23 @@ int batch_tile_dims(int* w, int* h) {
     return kBatchThreads;
 }
 
+void batch_box_dims(int* bx, int* by) {
+    *bx = kBoxW;
+    *by = kBoxH;
+}
+
 template <int TM>
 cudaError_t launch_batch(const BatchProb* probs, const int4* tiles, int ntiles, int nsteps, long long* level,
                          unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid, cudaStream_t st) {
     auto kern = k_batch<TM>;
+    cudaError_t e = allow_smem<k_batch<TM>>(kBatchSmem);
+    if (e != cudaSuccess) return e;
     void* args[] = {(void*)&probs, (void*)&tiles, (void*)&ntiles, (void*)&nsteps,
                     (void*)&level,  (void*)&bar_count, (void*)&bar_gen, (void*)&status};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(kBatchThreads);
-    cfg.dynamicSmemBytes = 0;
+    cfg.dynamicSmemBytes = kBatchSmem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
@@ -167,7 +206,8 @@ int batch_max_grid() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<TM>, kBatchThreads, 0);
+    allow_smem<k_batch<TM>>(kBatchSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<TM>, kBatchThreads, kBatchSmem);
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 

@@ -100,12 +100,14 @@ cudaError_t launch_feq_vjp(const S* r, const S* ux, const S* uy, const S* T, con
                            S* gy, S* gT, const Model<S>& M, long long n, cudaStream_t st);
 
 // Batch (lbm_batch.cu): FP32 problems advanced by one cooperative launch.
-struct BatchProb {
-    float* f[2];  // the two levels; level k lives in f[k & 1]
+struct alignas(64) BatchProb {
+    CUtensorMap tm[2];  // tensor maps of the two levels (box: batch_box_dims x 9)
+    float* f[2];        // the two levels; level k lives in f[k & 1]
     Model<float> M;
     Grid<float> G;
 };
 int batch_tile_dims(int* w, int* h);  // returns threads per CTA
+void batch_box_dims(int* bx, int* by);
 template <int TM>
 cudaError_t launch_batch(const BatchProb* probs, const int4* tiles, int ntiles, int nsteps, long long* level,
                          unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid, cudaStream_t st);
