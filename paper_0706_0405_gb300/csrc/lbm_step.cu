@@ -67,17 +67,26 @@ cudaError_t launch_vec(const float* fin, float* fout, const Model<float>& M, con
 // as single floats, and writes 8-byte pairs (no global loads, no per-load
 // 64-bit address arithmetic).  Waits are bounded: on give-up the CTA raises
 // ST_TIMEOUT, drains its copies in flight and returns.
-constexpr int kTileX = 64, kTileY = 8;
+#ifndef LBM_TILE_Y
+#define LBM_TILE_Y 8
+#endif
+constexpr int kTileX = 64, kTileY = LBM_TILE_Y;
 constexpr int kTileThreads = (kTileX / 2) * kTileY;
 constexpr int kBoxX = kTileX + 8, kBoxY = kTileY + 2;
 constexpr int kBoxFloats = kBoxX * kBoxY * 9;
 constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages start on 128-byte boundaries
-constexpr size_t kTileSmem = 128 + sizeof(float) * 2 * kStageFloats + 2 * sizeof(uint64_t);
 
-// Resident CTAs per SM the register budget is set for (3: 80 registers).
+// Shared-memory stages per CTA (boxes in flight + the one being computed) and
+// the resident CTAs per SM the register budget is set for.
+#ifndef LBM_TILE_STAGES
+#define LBM_TILE_STAGES 2
+#endif
 #ifndef LBM_TILE_MIN_BLOCKS
 #define LBM_TILE_MIN_BLOCKS 3
 #endif
+constexpr int kStages = LBM_TILE_STAGES;
+static_assert(kStages >= 2 && kStages <= 8, "2 to 8 stages");
+constexpr size_t kTileSmem = 128 + sizeof(float) * kStages * kStageFloats + kStages * sizeof(uint64_t);
 
 template <int TM>
 __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
@@ -87,12 +96,11 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
     // tensor copies need a 128-byte aligned destination: align the base here
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
     float* box = reinterpret_cast<float*>(smem);
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(float) * 2 * kStageFloats);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(float) * kStages * kStageFloats);
     __shared__ int abort_flag;
     const int tid = threadIdx.x, tx = tid % (kTileX / 2), ty = tid / (kTileX / 2);
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int j = 0; j < kStages; ++j) mbar_init(&bar[j], 1);
         fence_mbar_init();
         abort_flag = 0;
     }
@@ -103,11 +111,17 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
         // array column x0 is interior column x0 - 4; array row y0 is interior row y0 - 1
         tma_load_3d(box + stage * kStageFloats, &tmap, x0, y0, 0, &bar[stage]);
     };
-    auto wait = [&](int k) { return mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), kWaitLimit); };
+    // local tile k of this CTA lives in stage k % kStages; its phase parity
+    // is (k / kStages) & 1
+    auto wait = [&](int k) {
+        return mbar_wait_bounded(&bar[k % kStages], (uint32_t)((k / kStages) & 1), kWaitLimit);
+    };
     int issued = -1, waited = -1;  // local tile indices (same in every thread)
-    if (blockIdx.x < ntiles) {
-        if (tid == 0) issue(blockIdx.x, 0);
-        issued = 0;
+    for (int j = 0; j < kStages - 1; ++j) {  // fill all stages but one
+        const int t = blockIdx.x + j * gridDim.x;
+        if (t >= ntiles) break;
+        if (tid == 0) issue(t, j);
+        issued = j;
     }
     const size_t pl = (size_t)G.plane;
     constexpr int P = kBoxX * kBoxY;  // floats per plane in the box
@@ -126,15 +140,18 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
             return;
         }
         waited = k;
-        if (t + (int)gridDim.x < ntiles) {
-            if (tid == 0) issue(t + gridDim.x, (k + 1) & 1);
-            issued = k + 1;
+        {  // the stage of tile k - 1 now takes tile k + kStages - 1
+            const int kn = k + kStages - 1, tn = blockIdx.x + kn * gridDim.x;
+            if (tn < ntiles) {
+                if (tid == 0) issue(tn, kn % kStages);
+                issued = kn;
+            }
         }
         const int ix0 = (t % tiles_x) * kTileX + 2 * tx, iy = (t / tiles_x) * kTileY + ty;
         if (ix0 >= G.nx || iy >= G.ny) continue;
         const int nvalid = min(2, G.nx - ix0);
         // centre of node ix0 in the box: row ty + 1, column 2 tx + 4 (8-byte aligned)
-        const float* b = box + (k & 1) * kStageFloats + (ty + 1) * kBoxX + (2 * tx + 4);
+        const float* b = box + (k % kStages) * kStageFloats + (ty + 1) * kBoxX + (2 * tx + 4);
         float2 C[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) C[i] = *reinterpret_cast<const float2*>(b + i * P);
