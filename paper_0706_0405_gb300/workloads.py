@@ -202,7 +202,8 @@ DMR_X0 = 1.0 / 6.0                   # where the shock meets the wall at t = 0
 
 
 def dmr(ny: int = 1024, alpha: float = 0.1, lam_scale: float = 2.0, t_end: float = 0.2,
-        steps: int | None = None, c1: float = 10.0, c2: float = 20.0, eta0: float = 15.0) -> Problem:
+        steps: int | None = None, c1: float = 10.0, c2: float = 20.0, eta0: float = 15.0,
+        x0: float = DMR_X0, dt: float | None = None) -> Problem:
     """Double Mach reflection of a Mach-10 shock (Sec. 4.2, Fig. 12), in the
     [0, 4] x [0, 1] geometry with the reflecting wall from x = 1/6 and the shock
     at 60 degrees to the wall, dx = 1/ny, dt = 0.1 dx / c2, to t = 0.2.
@@ -214,24 +215,38 @@ def dmr(ny: int = 1024, alpha: float = 0.1, lam_scale: float = 2.0, t_end: float
     Left: Dirichlet post-shock.  Right: zero-gradient outflow.  Bottom:
     Dirichlet post-shock for x < 1/6, reflecting wall beyond.  Top: the exact
     shock position x_s(t) = 1/6 + (y + 20 t) / sqrt(3) at the ghost row's
-    height, post-shock state before it and pre-shock state after it."""
+    height, post-shock state before it and pre-shock state after it.  ``x0``
+    moves the wall start (and the shock's foot); ``dt`` overrides alpha."""
     nx, dx = 4 * ny, 1.0 / ny
-    dt = alpha * dx / c2
+    if dt is None:
+        dt = alpha * dx / c2
     post, pre = _ptoT(DMR_POST), _ptoT(DMR_PRE)
     s3 = math.sqrt(3.0)
     y_ghost_top = (ny + 0.5) * dx
     sides = (
         Side("dirichlet", state_lo=post, state_hi=post),
         Side("outflow"),
-        Side("dirichlet", "reflect", DMR_X0, 0.0, post, post),
-        Side("dirichlet", "dirichlet", DMR_X0 + y_ghost_top / s3, 2.0 * DMR_SHOCK_SPEED / s3,
+        Side("dirichlet", "reflect", x0, 0.0, post, post),
+        Side("dirichlet", "dirichlet", x0 + y_ghost_top / s3, 2.0 * DMR_SHOCK_SPEED / s3,
              post, pre),
     )
     n = int(round(t_end / dt)) if steps is None else steps
     return Problem(f"dmr_{nx}x{ny}", nx, ny, B_AIR, dt, dt, dx, c1, c2, eta0, 0.25,
                    lambda_eq13(c1, dx, lam_scale), sides, n,
-                   {"kind": "dmr", "pre": pre, "post": post, "x0": DMR_X0,
+                   {"kind": "dmr", "pre": pre, "post": post, "x0": x0,
                     "slope": 1.0 / s3})
+
+
+def dmr_paper(alpha: float = 0.1, lam_scale: float = 2.0, t_end: float = 0.2, steps: int | None = None,
+              c1: float = 10.0, c2: float = 20.0, eta0: float = 15.0, dt: float | None = None) -> Problem:
+    """The paper's own double-Mach-reflection run (Sec. 4.2, Fig. 12):
+    dx = dy = 0.01 on [0, 4] x [0, 1] (400 x 100 cells) with the reflecting
+    wall from 20 mesh lengths (x = 0.2).  The paper's constants c1 = 8,
+    c2 = 16, eta0 = 10, dt = 2e-4 can be passed; by default the vetted set of
+    ``dmr`` is used, to the Woodward-Colella time t = 0.2."""
+    p = dmr(100, alpha=alpha, lam_scale=lam_scale, t_end=t_end, steps=steps, c1=c1, c2=c2, eta0=eta0,
+            x0=0.2, dt=dt)
+    return replace(p, name="dmr_paper_400x100")
 
 
 def regular_reflection(ny: int = 300, alpha: float = 0.1, lam_scale: float = 2.0,

@@ -53,7 +53,7 @@ def _measures(p, r, T):
     return xl, xr, width, dT.min(), dT.max()
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32_tdf"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32_tdf", "fp32_cons"])
 def test_mach30_matches_exact_solution(prec):
     p = W.mach30_fig8()
     r, ux, T, flags = _run(p, prec)

@@ -46,7 +46,7 @@ def _crossing(profile, level, dx):
     return (k - 0.5 + (level - profile[k - 1]) / (profile[k] - profile[k - 1])) * dx
 
 
-@pytest.mark.parametrize("prec", ["fp64", "fp32_tdf"])
+@pytest.mark.parametrize("prec", ["fp64", "fp32_tdf", "fp32_cons"])
 def test_regular_reflection_matches_exact_solution(prec):
     p, rho, x_wall, slope = _exact()
     with lbm.Lattice(p, prec) as lat:

@@ -249,3 +249,18 @@ def test_step_nodes_matches_full_step():
     out = oracle.step_nodes(p, f.copy(), 7, nodes)
     gi = oracle.interior(g).reshape(9, -1)
     assert np.array_equal(out, gi[:, nodes].T)
+
+
+def test_paper_dmr_constants_go_nonphysical_but_the_vetted_set_does_not():
+    """Sec. 4.2, Fig. 12: on the paper's 400 x 100 grid with the wall from 20
+    mesh lengths, its constants (c1 = 8, c2 = 16, eta0 = 10, dt = 2e-4,
+    lambda of Eq. 13) leave nodes with rho <= 0 or T <= 0 within 200 steps
+    (t = 0.04); the vetted set (c1 = 10, c2 = 20, eta0 = 15, alpha = 0.1,
+    lambda = 2 x Eq. 13) runs the same 0.04 in time cleanly."""
+    oracle.set_threads(oracle.max_threads())
+    bad = W.dmr_paper(c1=8.0, c2=16.0, eta0=10.0, dt=2e-4, lam_scale=1.0, steps=200)
+    f = oracle.init(bad, *W.initial_fields(bad))
+    assert oracle.run(bad, f, bad.steps) > 0
+    good = W.dmr_paper(t_end=0.04)
+    f = oracle.init(good, *W.initial_fields(good))
+    assert oracle.run(good, f, good.steps) == 0
