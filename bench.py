@@ -328,6 +328,7 @@ def extras(args, p, fields, stream):
     with lbm.Batch(probs, args.precision) as bt:
         bt.init(bfields).step(10)
         bt.sync()
+        bshape, bshape_ms = bt.autotune(steps=20)
         bt.init(bfields)
         torch.cuda.synchronize()
         s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -355,6 +356,11 @@ def extras(args, p, fields, stream):
                     "GLUPS": round(nodes * steps / bsecs / 1e9, 3),
                     "separate_launches_GLUPS": round(nodes * steps / ssecs / 1e9, 3),
                     "speedup": round(ssecs / bsecs, 2), "grid": grid, "tiles_per_step": ntiles,
+                    "autotuned": {"nodes_per_thread": bshape[0], "grid": bshape[1],
+                                  "candidates_ms_per_step": [round(m, 4) for m in bshape_ms]},
+                    "hbm_GBs": round(BYTES_PER_NODE[args.precision] * nodes * steps / bsecs / 1e9, 1),
+                    "hbm_frac": round(BYTES_PER_NODE[args.precision] * nodes * steps / bsecs / 1e9
+                                      / hbm_peak()[0], 4),
                     "cuda_graph": bool(graph),
                     "working_set_MB": round(sum(2 * 9 * (b.ny + 2) * ((b.nx + 8 + 31) // 32 * 32) * 4
                                                 for b in probs) / 1e6, 1)}

@@ -1074,6 +1074,8 @@ struct lbm_batch {
     long long step = 0;
     bool ready = false;
     int grid = 0;
+    int npt = 1;                  // nodes per thread of the batch kernel (1 or 2)
+    int max_grid[3] = {0, 0, 0};  // resident CTAs of a full wave, per npt
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_n = -1;
@@ -1094,7 +1096,7 @@ cudaError_t batch_launch(lbm_batch* b, int n) {
     auto go = [&](auto tm) {
         constexpr int TM = decltype(tm)::value;
         return launch_batch<TM>(b->d_probs, b->d_tiles, b->ntiles, n, b->d_level, b->d_bar, b->d_bar + 1,
-                                b->d_status, b->grid, b->stream);
+                                b->d_status, b->grid, b->npt, b->stream);
     };
     switch (b->prec) {
     case LBM_FP32_T64: return go(std::integral_constant<int, T_INT64>{});
@@ -1195,11 +1197,13 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
         lbm_batch_destroy(b);
         return bfail(nullptr, e == cudaErrorMemoryAllocation ? LBM_E_NOMEM : LBM_E_CUDA, m);
     }
-    int maxg = prec == LBM_FP32_T64    ? batch_max_grid<T_INT64>()
-               : prec == LBM_FP32_TDF  ? batch_max_grid<T_DF>()
-               : prec == LBM_FP32_CONS ? batch_max_grid<T_CONS>()
-                                       : batch_max_grid<T_INT32>();
-    b->grid = maxg < b->ntiles ? maxg : b->ntiles;
+    for (int npt = 1; npt <= 2; ++npt)
+        b->max_grid[npt] = prec == LBM_FP32_T64    ? batch_max_grid<T_INT64>(npt)
+                           : prec == LBM_FP32_TDF  ? batch_max_grid<T_DF>(npt)
+                           : prec == LBM_FP32_CONS ? batch_max_grid<T_CONS>(npt)
+                                                   : batch_max_grid<T_INT32>(npt);
+    b->npt = 1;
+    b->grid = b->max_grid[1] < b->ntiles ? b->max_grid[1] : b->ntiles;
     *out = b;
     return LBM_OK;
 }
@@ -1391,6 +1395,133 @@ lbm_status lbm_vn_scan(const lbm_vn_case* cases, int ncases, const int* dirs, in
         e = cudaMemcpyAsync(growth, d_g, sizeof(double) * (size_t)ncases, cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess && ((radius && !r_dev) || (growth && !g_dev))) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return cuda_fail(nullptr, e, "lbm_vn_scan");
+    return LBM_OK;
+}
+
+}  // extern "C"
+
+// ------------------------------------------------------- batch launch shape
+namespace {
+void batch_drop_graph(lbm_batch* b) {
+    if (b->exec) cudaGraphExecDestroy(b->exec);
+    if (b->graph) cudaGraphDestroy(b->graph);
+    b->exec = nullptr;
+    b->graph = nullptr;
+    b->graph_n = -1;
+    if (b->graph_state > 0) b->graph_state = 0;
+}
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_set_launch(lbm_batch* b, const lbm_batch_launch* l) {
+    if (!b || !l) return bfail(b, LBM_E_INVAL, "lbm_batch_set_launch: NULL argument");
+    if (l->npt != 1 && l->npt != 2) return bfail(b, LBM_E_INVAL, "lbm_batch_set_launch: npt must be 1 or 2");
+    const int full = b->max_grid[l->npt] < b->ntiles ? b->max_grid[l->npt] : b->ntiles;
+    if (l->grid < 0 || l->grid > full)
+        return bfail(b, LBM_E_INVAL, "lbm_batch_set_launch: grid must lie in [0, " + std::to_string(full) + "]");
+    cudaSetDevice(b->device);
+    cudaStreamSynchronize(b->stream);
+    b->npt = l->npt;
+    b->grid = l->grid == 0 ? full : l->grid;
+    batch_drop_graph(b);
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_get_launch(const lbm_batch* b, lbm_batch_launch* l) {
+    if (!b || !l) return LBM_E_INVAL;
+    l->npt = b->npt;
+    l->grid = b->grid;
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_autotune(lbm_batch* b, int steps, lbm_batch_launch* best, double* ms, int* n_candidates) {
+    if (!b) return bfail(nullptr, LBM_E_INVAL, "NULL batch");
+    if (steps < 1) return bfail(b, LBM_E_INVAL, "lbm_batch_autotune: steps must be >= 1");
+    if (!b->ready) return bfail(b, LBM_E_STATE, "lbm_batch_autotune before lbm_batch_init");
+    cudaSetDevice(b->device);
+    // candidates: nodes per thread 1 or 2, a full wave or half of one
+    lbm_batch_launch cand[4];
+    int nc = 0;
+    for (int npt = 1; npt <= 2; ++npt) {
+        const int full = b->max_grid[npt] < b->ntiles ? b->max_grid[npt] : b->ntiles;
+        cand[nc++] = {npt, full};
+        if (full >= 2) cand[nc++] = {npt, full / 2};
+    }
+    // save every problem's current level, the level counter and the status
+    const int cur = (int)(b->step & 1);
+    size_t total = 0;
+    for (lbm_ctx* c : b->ctx) total += level_bytes(c);
+    unsigned char* save = nullptr;
+    long long* d_lsave = nullptr;
+    unsigned* d_ssave = nullptr;
+    cudaError_t e = cudaMalloc((void**)&save, total);
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_lsave, sizeof(long long));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&d_ssave, sizeof(unsigned));
+    size_t off = 0;
+    for (lbm_ctx* c : b->ctx) {
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(save + off, c->f[cur], level_bytes(c), cudaMemcpyDeviceToDevice, b->stream);
+        off += level_bytes(c);
+    }
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_lsave, b->d_level, sizeof(long long), cudaMemcpyDeviceToDevice, b->stream);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(d_ssave, b->d_status, sizeof(unsigned), cudaMemcpyDeviceToDevice, b->stream);
+    auto restore = [&]() {
+        cudaError_t r = cudaSuccess;
+        size_t o = 0;
+        for (lbm_ctx* c : b->ctx) {
+            if (r == cudaSuccess)
+                r = cudaMemcpyAsync(c->f[cur], save + o, level_bytes(c), cudaMemcpyDeviceToDevice, b->stream);
+            o += level_bytes(c);
+        }
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(b->d_level, d_lsave, sizeof(long long), cudaMemcpyDeviceToDevice, b->stream);
+        if (r == cudaSuccess)
+            r = cudaMemcpyAsync(b->d_status, d_ssave, sizeof(unsigned), cudaMemcpyDeviceToDevice, b->stream);
+        return r;
+    };
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (e == cudaSuccess) e = cudaEventCreate(&t0);
+    if (e == cudaSuccess) e = cudaEventCreate(&t1);
+    const int keep_npt = b->npt, keep_grid = b->grid;
+    int bi = -1;
+    float bms = 0.0f;
+    for (int k = 0; k < nc && e == cudaSuccess; ++k) {
+        b->npt = cand[k].npt;
+        b->grid = cand[k].grid;
+        e = batch_launch(b, 1);  // untimed: first launch of the variant
+        if (e == cudaSuccess) e = restore();
+        if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
+        if (e == cudaSuccess) e = batch_launch(b, steps);
+        if (e == cudaSuccess) e = cudaEventRecord(t1, b->stream);
+        if (e == cudaSuccess) e = cudaEventSynchronize(t1);
+        float m = 0.0f;
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&m, t0, t1);
+        if (e == cudaSuccess) e = restore();
+        if (e == cudaSuccess && ms) ms[k] = m / steps;
+        if (e == cudaSuccess && (bi < 0 || m < bms)) {
+            bi = k;
+            bms = m;
+        }
+    }
+    if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);
+    if (t0) cudaEventDestroy(t0);
+    if (t1) cudaEventDestroy(t1);
+    cudaFree(save);
+    cudaFree(d_lsave);
+    cudaFree(d_ssave);
+    if (e != cudaSuccess || bi < 0) {
+        b->npt = keep_npt;
+        b->grid = keep_grid;
+        return bfail(b, LBM_E_CUDA, std::string("lbm_batch_autotune: ") + cudaGetErrorString(e));
+    }
+    b->npt = cand[bi].npt;
+    b->grid = cand[bi].grid;
+    batch_drop_graph(b);
+    if (best) *best = cand[bi];
+    if (n_candidates) *n_candidates = nc;
     return LBM_OK;
 }
 

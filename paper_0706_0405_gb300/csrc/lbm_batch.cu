@@ -13,9 +13,13 @@
 namespace lbm {
 
 namespace {
-constexpr int kBatchThreads = 256;
-constexpr int kTileW = 64;  // columns per tile (one node per thread)
+constexpr int kTileW = 64;  // columns per tile
 constexpr int kTileH = 4;   // rows per tile
+// threads per CTA for NPT x-adjacent nodes per thread (1 or 2)
+template <int NPT>
+constexpr int batch_threads() {
+    return kTileW / NPT * kTileH;
+}
 constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz, then give up
 constexpr uint32_t kBatchWaitLimit = 1u << 22;       // mbarrier probes before a wait gives up
 
@@ -67,8 +71,8 @@ constexpr int kBoxFloats = 9 * kBoxPlane;
 constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages on 128-byte boundaries
 constexpr size_t kBatchSmem = 128 + sizeof(float) * 2 * kStageFloats + 2 * sizeof(uint64_t);
 
-template <int TM>
-__global__ void __launch_bounds__(kBatchThreads)
+template <int TM, int NPT>
+__global__ void __launch_bounds__(batch_threads<NPT>())
     k_batch(const BatchProb* __restrict__ probs, const int4* __restrict__ tiles, int ntiles, int nsteps,
             long long* level_ptr, unsigned* bar_count, unsigned* bar_gen, unsigned* status) {
     __shared__ Model<float> sM;
@@ -88,7 +92,8 @@ __global__ void __launch_bounds__(kBatchThreads)
     __syncthreads();
     const long long level0 = *(volatile long long*)level_ptr;
     unsigned bits = 0;
-    const int r = tid / kTileW, cx = tid % kTileW;
+    constexpr int kLanesX = kTileW / NPT;  // threads along a tile row
+    const int r = tid / kLanesX, cx = tid % kLanesX;
     // a contiguous run of tiles per CTA: consecutive tiles mostly share a
     // problem, so its constants are copied to shared memory rarely
     const int per = (ntiles + gridDim.x - 1) / gridDim.x;
@@ -137,29 +142,82 @@ __global__ void __launch_bounds__(kBatchThreads)
                 cur = T.x;
                 __syncthreads();
             }
-            const int ix = T.y + cx, iy = T.z + r;
-            if (ix < sG.nx && iy < sG.ny) {
-                const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxW + (cx + 4);
-                float f[9];
+            if constexpr (NPT == 1) {
+                const int ix = T.y + cx, iy = T.z + r;
+                if (ix < sG.nx && iy < sG.ny) {
+                    const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxW + (cx + 4);
+                    float f[9];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) f[i] = b[i * kBoxPlane];
-                float rho, ux, uy, Tt;
-                moments<float, TM>(f, sM, rho, ux, uy, Tt);
-                bits |= health(rho, ux, uy, Tt);
-                float ofe[9], o[9];
-                relaxation<float, TM>(sM, f, rho, ux, uy, Tt, ofe);
+                    for (int i = 0; i < 9; ++i) f[i] = b[i * kBoxPlane];
+                    float rho, ux, uy, Tt;
+                    moments<float, TM>(f, sM, rho, ux, uy, Tt);
+                    bits |= health(rho, ux, uy, Tt);
+                    float ofe[9], o[9];
+                    relaxation<float, TM>(sM, f, rho, ux, uy, Tt, ofe);
 #pragma unroll
-                for (int i = 0; i < 9; ++i) {
-                    const float* bp = b + i * kBoxPlane;
-                    o[i] = update(sM, i, ofe[i], f[i], bp[1], bp[-1], bp[kBoxW], bp[-kBoxW]);
+                    for (int i = 0; i < 9; ++i) {
+                        const float* bp = b + i * kBoxPlane;
+                        o[i] = update(sM, i, ofe[i], f[i], bp[1], bp[-1], bp[kBoxW], bp[-kBoxW]);
+                    }
+                    float* fout = P.f[par ^ 1];
+                    const size_t pl = (size_t)sG.plane;
+                    const size_t c = cell(sG, ix, iy);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) fout[i * pl + c] = o[i];
+                    if (ix == 0 || iy == 0 || ix == sG.nx - 1 || iy == sG.ny - 1)
+                        write_ghosts(sG, fout, ix, iy, o, level + 1);
                 }
-                float* fout = P.f[par ^ 1];
-                const size_t pl = (size_t)sG.plane;
-                const size_t c = cell(sG, ix, iy);
+            } else {  // two x-adjacent nodes per thread, 8-byte shared loads and stores
+                const int ix0 = T.y + 2 * cx, iy = T.z + r;
+                if (ix0 < sG.nx && iy < sG.ny) {
+                    const int nvalid = min(2, sG.nx - ix0);
+                    const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxW + (2 * cx + 4);
+                    float2 C[9];
 #pragma unroll
-                for (int i = 0; i < 9; ++i) fout[i * pl + c] = o[i];
-                if (ix == 0 || iy == 0 || ix == sG.nx - 1 || iy == sG.ny - 1)
-                    write_ghosts(sG, fout, ix, iy, o, level + 1);
+                    for (int i = 0; i < 9; ++i) C[i] = *reinterpret_cast<const float2*>(b + i * kBoxPlane);
+                    float acc[9][2];
+#pragma unroll
+                    for (int j = 0; j < 2; ++j) {
+                        float f[9];
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) f[i] = j ? C[i].y : C[i].x;
+                        float rho, ux, uy, Tt;
+                        moments<float, TM>(f, sM, rho, ux, uy, Tt);
+                        if (j < nvalid) bits |= health(rho, ux, uy, Tt);
+                        float ofe[9];
+                        relaxation<float, TM>(sM, f, rho, ux, uy, Tt, ofe);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) acc[i][j] = ofe[i];
+                    }
+                    float* fout = P.f[par ^ 1];
+                    const size_t pl = (size_t)sG.plane;
+                    float* out = fout + cell(sG, ix0, iy);  // 8-byte aligned: ix0 + PADX is even
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const float* bp = b + i * kBoxPlane;
+                        const float2 Nn = *reinterpret_cast<const float2*>(bp + kBoxW);
+                        const float2 Ss = *reinterpret_cast<const float2*>(bp - kBoxW);
+                        const float Wv = bp[-1], Ev = bp[2];
+                        float2 o;
+                        o.x = update(sM, i, acc[i][0], C[i].x, C[i].y, Wv, Nn.x, Ss.x);
+                        o.y = update(sM, i, acc[i][1], C[i].y, Ev, C[i].x, Nn.y, Ss.y);
+                        if (nvalid == 2)
+                            *reinterpret_cast<float2*>(out + i * pl) = o;
+                        else
+                            out[i * pl] = o.x;
+                    }
+                    const bool edge_row = iy == 0 || iy == sG.ny - 1;
+                    if (edge_row || ix0 == 0 || ix0 + nvalid == sG.nx) {
+                        for (int j = 0; j < nvalid; ++j) {
+                            const int ix = ix0 + j;
+                            if (!(edge_row || ix == 0 || ix == sG.nx - 1)) continue;
+                            float v[9];
+#pragma unroll
+                            for (int i = 0; i < 9; ++i) v[i] = out[i * pl + j];
+                            write_ghosts(sG, fout, ix, iy, v, level + 1);
+                        }
+                    }
+                }
             }
         }
         if (!grid_barrier(bar_count, bar_gen, status)) return;
@@ -172,7 +230,7 @@ __global__ void __launch_bounds__(kBatchThreads)
 int batch_tile_dims(int* w, int* h) {
     *w = kTileW;
     *h = kTileH;
-    return kBatchThreads;
+    return batch_threads<1>();
 }
 
 void batch_box_dims(int* bx, int* by) {
@@ -180,17 +238,17 @@ void batch_box_dims(int* bx, int* by) {
     *by = kBoxH;
 }
 
-template <int TM>
-cudaError_t launch_batch(const BatchProb* probs, const int4* tiles, int ntiles, int nsteps, long long* level,
-                         unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid, cudaStream_t st) {
-    auto kern = k_batch<TM>;
-    cudaError_t e = allow_smem<k_batch<TM>>(kBatchSmem);
+template <int TM, int NPT>
+cudaError_t launch_batch_v(const BatchProb* probs, const int4* tiles, int ntiles, int nsteps, long long* level,
+                           unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid, cudaStream_t st) {
+    auto kern = k_batch<TM, NPT>;
+    cudaError_t e = allow_smem<k_batch<TM, NPT>>(kBatchSmem);
     if (e != cudaSuccess) return e;
     void* args[] = {(void*)&probs, (void*)&tiles, (void*)&ntiles, (void*)&nsteps,
                     (void*)&level,  (void*)&bar_count, (void*)&bar_gen, (void*)&status};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kBatchThreads);
+    cfg.blockDim = dim3(batch_threads<NPT>());
     cfg.dynamicSmemBytes = kBatchSmem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
@@ -202,26 +260,37 @@ cudaError_t launch_batch(const BatchProb* probs, const int4* tiles, int ntiles, 
 }
 
 template <int TM>
-int batch_max_grid() {
+cudaError_t launch_batch(const BatchProb* probs, const int4* tiles, int ntiles, int nsteps, long long* level,
+                         unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid, int npt,
+                         cudaStream_t st) {
+    if (npt == 2)
+        return launch_batch_v<TM, 2>(probs, tiles, ntiles, nsteps, level, bar_count, bar_gen, status, grid, st);
+    return launch_batch_v<TM, 1>(probs, tiles, ntiles, nsteps, level, bar_count, bar_gen, status, grid, st);
+}
+
+template <int TM, int NPT>
+int batch_max_grid_v() {
     int dev = 0, sms = 0, per_sm = 0;
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    allow_smem<k_batch<TM>>(kBatchSmem);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<TM>, kBatchThreads, kBatchSmem);
+    allow_smem<k_batch<TM, NPT>>(kBatchSmem);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch<TM, NPT>, batch_threads<NPT>(), kBatchSmem);
     return sms * (per_sm > 0 ? per_sm : 1);
 }
 
-template cudaError_t launch_batch<T_INT32>(const BatchProb*, const int4*, int, int, long long*, unsigned*,
-                                           unsigned*, unsigned*, int, cudaStream_t);
-template cudaError_t launch_batch<T_INT64>(const BatchProb*, const int4*, int, int, long long*, unsigned*,
-                                           unsigned*, unsigned*, int, cudaStream_t);
-template cudaError_t launch_batch<T_DF>(const BatchProb*, const int4*, int, int, long long*, unsigned*,
-                                        unsigned*, unsigned*, int, cudaStream_t);
-template cudaError_t launch_batch<T_CONS>(const BatchProb*, const int4*, int, int, long long*, unsigned*,
-                                          unsigned*, unsigned*, int, cudaStream_t);
-template int batch_max_grid<T_INT32>();
-template int batch_max_grid<T_INT64>();
-template int batch_max_grid<T_DF>();
-template int batch_max_grid<T_CONS>();
+template <int TM>
+int batch_max_grid(int npt) {
+    return npt == 2 ? batch_max_grid_v<TM, 2>() : batch_max_grid_v<TM, 1>();
+}
+
+#define LBM_BATCH_INST(TM)                                                                                  \
+    template cudaError_t launch_batch<TM>(const BatchProb*, const int4*, int, int, long long*, unsigned*,  \
+                                          unsigned*, unsigned*, int, int, cudaStream_t);                   \
+    template int batch_max_grid<TM>(int);
+LBM_BATCH_INST(T_INT32)
+LBM_BATCH_INST(T_INT64)
+LBM_BATCH_INST(T_DF)
+LBM_BATCH_INST(T_CONS)
+#undef LBM_BATCH_INST
 
 }  // namespace lbm

@@ -108,11 +108,14 @@ struct alignas(64) BatchProb {
 };
 int batch_tile_dims(int* w, int* h);  // returns threads per CTA
 void batch_box_dims(int* bx, int* by);
+// npt: nodes per thread (1: 256-thread CTAs; 2: 128-thread CTAs, two
+// x-adjacent nodes each).  grid must not exceed batch_max_grid(npt).
 template <int TM>
 cudaError_t launch_batch(const BatchProb* probs, const int4* tiles, int ntiles, int nsteps, long long* level,
-                         unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid, cudaStream_t st);
+                         unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid, int npt,
+                         cudaStream_t st);
 template <int TM>
-int batch_max_grid();
+int batch_max_grid(int npt);
 
 // von Neumann scan (lbm_vonneumann.cu): one case is the step's constants
 // (folded weights, omega, equilibrium coefficients) and a uniform state.

@@ -31,7 +31,8 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init", "lbm_step"
            "lbm_record", "lbm_adjoint_seed", "lbm_adjoint_step", "lbm_feq_vjp",
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_init",
            "lbm_batch_step", "lbm_batch_sync", "lbm_batch_problem", "lbm_batch_info",
-           "lbm_probe_rates", "lbm_vn_scan")
+           "lbm_probe_rates", "lbm_vn_scan", "lbm_batch_set_launch", "lbm_batch_get_launch",
+           "lbm_batch_autotune")
 LBM_FLAG_NONPHYSICAL, LBM_FLAG_TIMEOUT, LBM_FLAG_T_NONPOSITIVE = 1, 2, 4
 
 
@@ -59,6 +60,13 @@ class lbm_problem(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("b", ctypes.c_double),
                 ("tau", ctypes.c_double), ("dt", ctypes.c_double), ("dx", ctypes.c_double),
                 ("dvm", lbm_dvm), ("diss", lbm_dissipation), ("bc", lbm_bc * 4)]
+
+
+class lbm_batch_launch(ctypes.Structure):
+    _fields_ = [("npt", ctypes.c_int), ("grid", ctypes.c_int)]
+
+    def as_tuple(self):
+        return (self.npt, self.grid)
 
 
 class lbm_vn_case(ctypes.Structure):
@@ -131,6 +139,10 @@ def load():
                                       ctypes.POINTER(lbm_dvm), ctypes.POINTER(ctypes.c_double), _VP],
                                      ctypes.c_int),
         "lbm_get_launch": ([ctx, ctypes.POINTER(lbm_launch)], ctypes.c_int),
+        "lbm_batch_set_launch": ([_VP, ctypes.POINTER(lbm_batch_launch)], ctypes.c_int),
+        "lbm_batch_get_launch": ([_VP, ctypes.POINTER(lbm_batch_launch)], ctypes.c_int),
+        "lbm_batch_autotune": ([_VP, ctypes.c_int, ctypes.POINTER(lbm_batch_launch), ctypes.POINTER(ctypes.c_double),
+                                ctypes.POINTER(ctypes.c_int)], ctypes.c_int),
         "lbm_vn_scan": ([ctypes.POINTER(lbm_vn_case), ctypes.c_int, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                          ctypes.c_int, _VP, _VP, _VP], ctypes.c_int),
         "lbm_autotune": ([ctx, ctypes.c_int, ctypes.POINTER(lbm_launch),
@@ -390,6 +402,25 @@ def lbm_batch_problem(b, p):
     return load().lbm_batch_problem(b, int(p))
 
 
+def lbm_batch_set_launch(b, npt, grid=0):
+    return _bcheck(b, load().lbm_batch_set_launch(b, ctypes.byref(lbm_batch_launch(int(npt), int(grid)))))
+
+
+def lbm_batch_get_launch(b):
+    l = lbm_batch_launch()
+    _bcheck(b, load().lbm_batch_get_launch(b, ctypes.byref(l)))
+    return l.as_tuple()
+
+
+def lbm_batch_autotune(b, steps=10):
+    """Returns ((npt, grid) chosen, per-step ms of each candidate)."""
+    best = lbm_batch_launch()
+    ms = (ctypes.c_double * 4)()
+    n = ctypes.c_int(0)
+    _bcheck(b, load().lbm_batch_autotune(b, int(steps), ctypes.byref(best), ms, ctypes.byref(n)))
+    return best.as_tuple(), list(ms[:n.value])
+
+
 def lbm_batch_info(b):
     g, t, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
     _bcheck(b, load().lbm_batch_info(b, ctypes.byref(g), ctypes.byref(t), ctypes.byref(gr)))
@@ -470,6 +501,16 @@ class Batch:
 
     def info(self):
         return lbm_batch_info(self.handle)
+
+    def set_launch(self, npt: int, grid: int = 0):
+        lbm_batch_set_launch(self.handle, npt, grid)
+        return self
+
+    def get_launch(self):
+        return lbm_batch_get_launch(self.handle)
+
+    def autotune(self, steps: int = 10):
+        return lbm_batch_autotune(self.handle, steps)
 
     def moments(self, p: int):
         import torch

@@ -191,3 +191,51 @@ def test_fp32_tile_adjoint_matches_oracle_and_simple_kernel(sides):
         assert np.max(np.abs(abar - wi)) <= 2e-5 * scale, variant
         assert dtau == pytest.approx(want_tau, rel=1e-4), variant
     assert np.max(np.abs(out[3][0] - out[0][0])) <= 1e-6 * scale
+
+
+def _fields_from_states(p, states, z, sigma, xp):
+    """Initial fields of the Mach-3 tube as functions of its left and right
+    states (rho, u, T)_L, (rho, u, T)_R with the seeded perturbation z:
+    rho (1 + sigma z), u + sigma max(|u_L|, 1) z, T (1 + sigma z)."""
+    rL, uL, TL, rR, uR, TR = states
+    x, _ = W.centres(p)
+    left = x < p.setup["x_d"]
+    if xp.__name__ == "torch":
+        left = xp.as_tensor(left, device="cuda")
+    where = (lambda c, a, b: xp.where(c, a, b))
+    uscale = xp.clamp(xp.abs(uL), min=1.0) if xp.__name__ == "torch" else max(abs(uL), 1.0)
+    rho = where(left, rL, rR) * (1 + sigma * z[0])
+    ux = where(left, uL, uR) + sigma * uscale * z[1]
+    uy = 0.0 * rho + sigma * uscale * z[2]
+    T = where(left, TL, TR) * (1 + sigma * z[3])
+    return rho, ux, uy, T
+
+
+def test_mach3_gradient_wrt_left_and_right_states_against_finite_differences():
+    """The adjoint configuration (Mach-3 tube 2048 x 256, 1000 steps,
+    checkpoint every 50, 1 % seeded perturbation): dL/d(rho, u, T) of the
+    left and right Riemann states through the GPU adjoint and autograd equal
+    central differences of the FP64 forward run to 1e-4 relative."""
+    import torch
+    from paper_0706_0405_gb300 import autodiff
+    p = W.mach3_2048x256()
+    rng = np.random.Generator(np.random.PCG64(21))
+    z = [rng.standard_normal((p.ny, p.nx)) for _ in range(4)]
+    target = W.initial_fields(p, seed=1, sigma=0.01)[0]
+    L, R = p.setup["left"], p.setup["right"]
+    s0 = [L[0], L[1], L[3], R[0], R[1], R[3]]
+    st = [torch.tensor(v, dtype=torch.float64, device="cuda", requires_grad=True) for v in s0]
+    zt = [torch.tensor(a, device="cuda") for a in z]
+    fields = _fields_from_states(p, st, zt, 0.01, torch)
+    rho, _, _, _ = autodiff.run(p, *[f.contiguous() for f in fields], p.tau, p.steps, every=50)
+    loss = 0.5 * torch.sum((rho - torch.tensor(target, device="cuda")) ** 2)
+    loss.backward()
+    for k in range(6):
+        h = 1e-6 * max(1.0, abs(s0[k]))
+        sp, sm = list(s0), list(s0)
+        sp[k] += h
+        sm[k] -= h
+        fp = [np.ascontiguousarray(a) for a in _fields_from_states(p, sp, z, 0.01, np)]
+        fm = [np.ascontiguousarray(a) for a in _fields_from_states(p, sm, z, 0.01, np)]
+        fd = (_loss(p, fp, target) - _loss(p, fm, target)) / (2 * h)
+        assert st[k].grad.item() == pytest.approx(fd, rel=1e-4, abs=1e-8 * abs(loss.item())), k

@@ -60,3 +60,50 @@ def test_batch_argument_errors():
         with pytest.raises(lbm.LbmError) as ei:
             b.step(1)
         assert ei.value.status == lbm.LBM_E_STATE
+
+
+@pytest.mark.parametrize("shape", [(2, 0), (1, 7), (2, 3)])
+def test_every_batch_launch_shape_gives_the_same_bits(shape):
+    """Two nodes per thread (128-thread CTAs) and grids of a few CTAs walk the
+    same tiles with the same per-node arithmetic: the levels equal those of
+    the default shape (one node per thread, a full wave) bit for bit."""
+    probs = _subset()
+    fields = [W.initial_fields(p) for p in probs]
+    out = {}
+    for sh in [(1, 0), shape]:
+        with lbm.Batch(probs, "fp32_cons") as b:
+            b.init(fields).set_launch(*sh).step(120)
+            b.sync()
+            out[sh] = [b.get_f(k).cpu().numpy() for k in range(len(probs))]
+    for a, c in zip(out[(1, 0)], out[shape]):
+        assert np.array_equal(a, c)
+
+
+def test_batch_autotune_restores_state_and_picks_a_shape():
+    probs = _subset()
+    fields = [W.initial_fields(p) for p in probs]
+    with lbm.Batch(probs, "fp32_cons") as b:
+        b.init(fields).step(30)
+        (npt, grid), ms = b.autotune(steps=5)
+        assert len(ms) == 4 and all(m > 0 for m in ms)
+        assert (npt, grid) == b.get_launch() and npt in (1, 2) and grid > 0
+        b.step(40)
+        b.sync()
+        grid_info, _, graph = b.info()
+        got = [b.get_f(k).cpu().numpy() for k in range(len(probs))]
+    assert graph == 1 and grid_info == grid
+    with lbm.Batch(probs, "fp32_cons") as b:
+        b.init(fields).step(70)
+        b.sync()
+        want = [b.get_f(k).cpu().numpy() for k in range(len(probs))]
+    for a, c in zip(got, want):
+        assert np.array_equal(a, c)
+
+
+def test_batch_launch_shape_errors():
+    probs = _subset()[:2]
+    with lbm.Batch(probs, "fp32") as b:
+        for bad in [(3, 0), (1, -1), (2, 10 ** 6)]:
+            with pytest.raises(lbm.LbmError) as ei:
+                b.set_launch(*bad)
+            assert ei.value.status == lbm.LBM_E_INVAL
