@@ -18,7 +18,7 @@ Contents
     radius.
 ``gasdynamics.py``
     the exact Riemann solution of the Euler equations (Eq. e2) and
-    Rankine-Hugoniot jump relations, used to judge the oracle's runs.
+    Rankine-Hugoniot jump relations, used to check the oracle's runs.
 
 Problems are passed as any object with the attributes ``nx, ny, b, tau, dt,
 dx, c1, c2, eta0, beta, lam`` (9 values) and ``sides`` (4 objects with

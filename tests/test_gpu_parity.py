@@ -1,6 +1,6 @@
 """Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
 
-Error measures (also stated in the design doc):
+Error measures:
   * rho, T: max over nodes of |gpu - oracle| / |oracle|;
   * ux, uy: max |gpu - oracle| / U with U = max(max |u|, max sqrt(T)) of the
     oracle's fields (velocity errors relative to the flow's speed scale);
