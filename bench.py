@@ -357,6 +357,7 @@ def extras(args, p, fields, stream):
                     "separate_launches_GLUPS": round(nodes * steps / ssecs / 1e9, 3),
                     "speedup": round(ssecs / bsecs, 2), "grid": grid, "tiles_per_step": ntiles,
                     "autotuned": {"nodes_per_thread": bshape[0], "grid": bshape[1],
+                                  "steps_per_pass": max(1, bshape[2]),
                                   "candidates_ms_per_step": [round(m, 4) for m in bshape_ms]},
                     "hbm_GBs": round(BYTES_PER_NODE[args.precision] * nodes * steps / bsecs / 1e9, 1),
                     "hbm_frac": round(BYTES_PER_NODE[args.precision] * nodes * steps / bsecs / 1e9

@@ -354,23 +354,32 @@ lbm_status lbm_batch_info(const lbm_batch* batch, int* grid, int* ntiles, int* g
 /* Launch shape of the batch kernel: npt = nodes per thread (1: 256-thread
  * CTAs, one node each; 2: 128-thread CTAs, two x-adjacent nodes each, 8-byte
  * shared-memory accesses) and grid = CTAs of the cooperative launch (1 up to
- * the resident CTAs of a full wave, capped at the tile count; 0 = a full
- * wave).  Every shape computes the same bits.  Setting a shape drops the
- * captured graph (the next lbm_batch_step captures a new one). */
+ * the resident CTAs of a full wave, capped at the work-item count; 0 = a
+ * full wave).  block = 3, 5 or 7 selects temporal blocking instead (only for
+ * batches whose problems all have at most 8 rows and no periodic x sides):
+ * one pass advances a 128-column segment of a problem by `block` steps in
+ * shared memory (halo of `block` columns each side, recomputed), so DRAM
+ * traffic and grid barriers drop by that factor; npt is then ignored.
+ * block = 0 or 1 is the one-step tile kernel.  Every shape computes the same
+ * bits.  Setting a shape drops the captured graph (the next lbm_batch_step
+ * captures a new one). */
 typedef struct lbm_batch_launch {
     int npt;
     int grid;
+    int block;
 } lbm_batch_launch;
 
 lbm_status lbm_batch_set_launch(lbm_batch* batch, const lbm_batch_launch* launch);
 lbm_status lbm_batch_get_launch(const lbm_batch* batch, lbm_batch_launch* launch);
 
 /* Time each candidate shape -- npt 1 and 2, each with a full wave and half a
- * wave of CTAs -- for `steps` steps on the batch's own current state (after
- * one untimed step per shape), restore the state, the level counter and the
- * health flags, and keep the fastest.  best (may be NULL) receives it;
- * ms[0..n) (may be NULL, room for 4) the per-step milliseconds of each
- * candidate in that order; *n_candidates (may be NULL) their number.
+ * wave of CTAs, then (where the batch allows it) temporal blocking with 3, 5
+ * and 7 steps per pass on a full wave -- for `steps` steps on the batch's own
+ * current state (after one untimed step per shape), restore the state, the
+ * level counter and the health flags, and keep the fastest.  best (may be
+ * NULL) receives it; ms[0..n) (may be NULL, room for 8) the per-step
+ * milliseconds of each candidate in that order; *n_candidates (may be NULL)
+ * their number.
  * Allocates one copy of every problem's current level for the duration of
  * the call; synchronises the batch's stream. */
 lbm_status lbm_batch_autotune(lbm_batch* batch, int steps, lbm_batch_launch* best, double* ms,

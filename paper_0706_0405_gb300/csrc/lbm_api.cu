@@ -1076,6 +1076,12 @@ struct lbm_batch {
     int grid = 0;
     int npt = 1;                  // nodes per thread of the batch kernel (1 or 2)
     int max_grid[3] = {0, 0, 0};  // resident CTAs of a full wave, per npt
+    int block = 0;                // steps per pass of the temporal-blocking kernel (0: tile kernel)
+    bool tb_ok = false;           // every problem thin enough, none periodic in x
+    int rows_max = 0;
+    int4* d_segs = nullptr;
+    int nsegs = 0;
+    int tb_max_grid[8] = {0, 0, 0, 0, 0, 0, 0, 0};  // per odd steps-per-pass 3, 5, 7
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t exec = nullptr;
     int graph_n = -1;
@@ -1095,6 +1101,9 @@ lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& msg) {
 cudaError_t batch_launch(lbm_batch* b, int n) {
     auto go = [&](auto tm) {
         constexpr int TM = decltype(tm)::value;
+        if (b->block > 1)
+            return launch_batch_tb<TM>(b->d_probs, b->d_segs, b->nsegs, n, b->block, b->rows_max, b->d_level,
+                                       b->d_bar, b->d_bar + 1, b->d_status, b->grid, b->stream);
         return launch_batch<TM>(b->d_probs, b->d_tiles, b->ntiles, n, b->d_level, b->d_bar, b->d_bar + 1,
                                 b->d_status, b->grid, b->npt, b->stream);
     };
@@ -1120,6 +1129,7 @@ void lbm_batch_destroy(lbm_batch* b) {
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     cudaFree(b->d_probs);
     cudaFree(b->d_tiles);
+    cudaFree(b->d_segs);
     cudaFree(b->d_level);
     cudaFree(b->d_bar);
     cudaFree(b->d_status);
@@ -1160,6 +1170,22 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
         for (int y0 = 0; y0 < probs[p].ny; y0 += th)
             for (int x0 = 0; x0 < probs[p].nx; x0 += tw) tiles.push_back(make_int4(p, x0, y0, 0));
     b->ntiles = (int)tiles.size();
+    // temporal blocking: thin problems without periodic x sides
+    b->tb_ok = true;
+    for (int p = 0; p < nprob && b->tb_ok; ++p) {
+        b->rows_max = probs[p].ny > b->rows_max ? probs[p].ny : b->rows_max;
+        if (probs[p].ny > kBatchTbRowsMax) b->tb_ok = false;
+        for (int side = LBM_SIDE_LEFT; side <= LBM_SIDE_RIGHT; ++side)
+            if (probs[p].bc[side].kind_lo == LBM_BC_PERIODIC || probs[p].bc[side].kind_hi == LBM_BC_PERIODIC)
+                b->tb_ok = false;
+    }
+    std::vector<int4> segs;
+    if (b->tb_ok) {
+        const int sw = batch_tb_width();
+        for (int p = 0; p < nprob; ++p)
+            for (int x0 = 0; x0 < probs[p].nx; x0 += sw) segs.push_back(make_int4(p, x0, 0, 0));
+    }
+    b->nsegs = (int)segs.size();
     std::vector<BatchProb> hp(nprob);
     int bbx = 0, bby = 0;
     batch_box_dims(&bbx, &bby);
@@ -1176,6 +1202,7 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
     }
     cudaError_t e = cudaMalloc((void**)&b->d_probs, sizeof(BatchProb) * nprob);
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles, sizeof(int4) * tiles.size());
+    if (e == cudaSuccess && b->tb_ok) e = cudaMalloc((void**)&b->d_segs, sizeof(int4) * segs.size());
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_level, sizeof(long long));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_bar, 2 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, sizeof(unsigned));
@@ -1188,6 +1215,8 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
     if (e == cudaSuccess)
         e = cudaMemcpyAsync(b->d_tiles, tiles.data(), sizeof(int4) * tiles.size(), cudaMemcpyHostToDevice,
                             b->stream);
+    if (e == cudaSuccess && b->tb_ok)
+        e = cudaMemcpyAsync(b->d_segs, segs.data(), sizeof(int4) * segs.size(), cudaMemcpyHostToDevice, b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), b->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(b->d_level, 0, sizeof(long long), b->stream);
@@ -1204,6 +1233,12 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
                                                    : batch_max_grid<T_INT32>(npt);
     b->npt = 1;
     b->grid = b->max_grid[1] < b->ntiles ? b->max_grid[1] : b->ntiles;
+    if (b->tb_ok)
+        for (int ns = 3; ns <= 7; ns += 2)
+            b->tb_max_grid[ns] = prec == LBM_FP32_T64    ? batch_tb_max_grid<T_INT64>(ns, b->rows_max)
+                                 : prec == LBM_FP32_TDF  ? batch_tb_max_grid<T_DF>(ns, b->rows_max)
+                                 : prec == LBM_FP32_CONS ? batch_tb_max_grid<T_CONS>(ns, b->rows_max)
+                                                         : batch_tb_max_grid<T_INT32>(ns, b->rows_max);
     *out = b;
     return LBM_OK;
 }
@@ -1416,13 +1451,27 @@ extern "C" {
 
 lbm_status lbm_batch_set_launch(lbm_batch* b, const lbm_batch_launch* l) {
     if (!b || !l) return bfail(b, LBM_E_INVAL, "lbm_batch_set_launch: NULL argument");
-    if (l->npt != 1 && l->npt != 2) return bfail(b, LBM_E_INVAL, "lbm_batch_set_launch: npt must be 1 or 2");
-    const int full = b->max_grid[l->npt] < b->ntiles ? b->max_grid[l->npt] : b->ntiles;
+    int full = 0;
+    if (l->block > 1) {
+        if (l->block != 3 && l->block != 5 && l->block != 7)
+            return bfail(b, LBM_E_INVAL, "lbm_batch_set_launch: block must be 0, 1, 3, 5 or 7");
+        if (!b->tb_ok)
+            return bfail(b, LBM_E_INVAL,
+                         "lbm_batch_set_launch: temporal blocking needs problems of at most " +
+                             std::to_string(kBatchTbRowsMax) + " rows and no periodic x sides");
+        full = b->tb_max_grid[l->block] < b->nsegs ? b->tb_max_grid[l->block] : b->nsegs;
+        if (full < 1) return bfail(b, LBM_E_INVAL, "lbm_batch_set_launch: the blocking kernel does not fit");
+    } else {
+        if (l->block < 0) return bfail(b, LBM_E_INVAL, "lbm_batch_set_launch: block must be 0, 1, 3, 5 or 7");
+        if (l->npt != 1 && l->npt != 2) return bfail(b, LBM_E_INVAL, "lbm_batch_set_launch: npt must be 1 or 2");
+        full = b->max_grid[l->npt] < b->ntiles ? b->max_grid[l->npt] : b->ntiles;
+    }
     if (l->grid < 0 || l->grid > full)
         return bfail(b, LBM_E_INVAL, "lbm_batch_set_launch: grid must lie in [0, " + std::to_string(full) + "]");
     cudaSetDevice(b->device);
     cudaStreamSynchronize(b->stream);
-    b->npt = l->npt;
+    b->block = l->block > 1 ? l->block : 0;
+    b->npt = l->block > 1 ? 1 : l->npt;
     b->grid = l->grid == 0 ? full : l->grid;
     batch_drop_graph(b);
     return LBM_OK;
@@ -1432,6 +1481,7 @@ lbm_status lbm_batch_get_launch(const lbm_batch* b, lbm_batch_launch* l) {
     if (!b || !l) return LBM_E_INVAL;
     l->npt = b->npt;
     l->grid = b->grid;
+    l->block = b->block;
     return LBM_OK;
 }
 
@@ -1441,13 +1491,18 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps, lbm_batch_launch* best, d
     if (!b->ready) return bfail(b, LBM_E_STATE, "lbm_batch_autotune before lbm_batch_init");
     cudaSetDevice(b->device);
     // candidates: nodes per thread 1 or 2, a full wave or half of one
-    lbm_batch_launch cand[4];
+    lbm_batch_launch cand[8];
     int nc = 0;
     for (int npt = 1; npt <= 2; ++npt) {
         const int full = b->max_grid[npt] < b->ntiles ? b->max_grid[npt] : b->ntiles;
-        cand[nc++] = {npt, full};
-        if (full >= 2) cand[nc++] = {npt, full / 2};
+        cand[nc++] = {npt, full, 0};
+        if (full >= 2) cand[nc++] = {npt, full / 2, 0};
     }
+    if (b->tb_ok)
+        for (int ns = 3; ns <= 7; ns += 2) {
+            const int full = b->tb_max_grid[ns] < b->nsegs ? b->tb_max_grid[ns] : b->nsegs;
+            if (full >= 1) cand[nc++] = {1, full, ns};
+        }
     // save every problem's current level, the level counter and the status
     const int cur = (int)(b->step & 1);
     size_t total = 0;
@@ -1485,12 +1540,13 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps, lbm_batch_launch* best, d
     cudaEvent_t t0 = nullptr, t1 = nullptr;
     if (e == cudaSuccess) e = cudaEventCreate(&t0);
     if (e == cudaSuccess) e = cudaEventCreate(&t1);
-    const int keep_npt = b->npt, keep_grid = b->grid;
+    const int keep_npt = b->npt, keep_grid = b->grid, keep_block = b->block;
     int bi = -1;
     float bms = 0.0f;
     for (int k = 0; k < nc && e == cudaSuccess; ++k) {
         b->npt = cand[k].npt;
         b->grid = cand[k].grid;
+        b->block = cand[k].block;
         e = batch_launch(b, 1);  // untimed: first launch of the variant
         if (e == cudaSuccess) e = restore();
         if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
@@ -1515,10 +1571,12 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps, lbm_batch_launch* best, d
     if (e != cudaSuccess || bi < 0) {
         b->npt = keep_npt;
         b->grid = keep_grid;
+        b->block = keep_block;
         return bfail(b, LBM_E_CUDA, std::string("lbm_batch_autotune: ") + cudaGetErrorString(e));
     }
     b->npt = cand[bi].npt;
     b->grid = cand[bi].grid;
+    b->block = cand[bi].block;
     batch_drop_graph(b);
     if (best) *best = cand[bi];
     if (n_candidates) *n_candidates = nc;

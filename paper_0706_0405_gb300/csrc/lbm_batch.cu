@@ -225,6 +225,168 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
     report(status, bits);
     if (blockIdx.x == 0 && threadIdx.x == 0) *level_ptr = level0 + nsteps;
 }
+// ------------------------------------------------- temporal blocking
+// For batches of thin problems (at most kTbRowsMax rows, no periodic x
+// sides) one pass advances a segment of kTbW columns (all rows) by NS steps
+// (NS odd) inside shared memory: it loads the level with a halo of NS columns
+// on each side (the ghost cells included), then each sub-step j updates the
+// columns within NS - 1 - j of the segment and fills the ghost cells of the
+// new level there by the same rules as write_ghosts, and the pass stores the
+// segment of level + NS, its ghost rows and, at a problem's ends, its ghost
+// columns.  NS odd puts level + NS in the other level buffer than the one the
+// pass reads, so no CTA overwrites data another is still loading; a grid
+// barrier separates passes.  The per-node arithmetic is that of every other
+// kernel, so the levels are bit-identical to stepping each problem alone;
+// DRAM traffic and grid barriers drop by a factor of NS for a redundant
+// update of (NS - 1) columns on each side of a segment.
+constexpr int kTbW = 128;
+constexpr int kTbThreads = 256;
+
+__host__ __device__ constexpr int tb_width(int ns) { return kTbW + 2 * ns; }
+
+// Value of a ghost cell of the level in buffer B (planes of rows_pitch rows of
+// width wb, row 0 = ghost row -1, column 0 = global column xo) for the level
+// `level`: pulled from the interior cell the rule makes it from.
+__device__ __forceinline__ void tb_ghost(const Grid<float>& G, float* B, int wb, int plane, int xo, int side,
+                                         int along, long long level) {
+    const int part = side_part(G, side, along, level);
+    const int kind = part ? G.kind_hi[side] : G.kind_lo[side];
+    int gx, gy, sx, sy;  // ghost cell and its source (global coordinates)
+    if (side == S_LEFT || side == S_RIGHT) {
+        gy = sy = along;
+        gx = side == S_LEFT ? -1 : G.nx;
+        sx = side == S_LEFT ? 0 : G.nx - 1;
+    } else {
+        gx = sx = along;
+        gy = side == S_BOTTOM ? -1 : G.ny;
+        sy = kind == BC_PERIODIC ? (side == S_BOTTOM ? G.ny - 1 : 0) : (side == S_BOTTOM ? 0 : G.ny - 1);
+    }
+    float* g = B + (gy + 1) * wb + (gx - xo);
+    const float* src = B + (sy + 1) * wb + (sx - xo);
+    if (kind == BC_DIRICHLET) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i * plane] = G.feq[side][part][i];
+    } else if (kind == BC_REFLECT) {
+        const bool xs = side == S_LEFT || side == S_RIGHT;
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i * plane] = src[(xs ? mirror_x(i) : mirror_y(i)) * plane];
+    } else {  // outflow copies the adjacent node; periodic (y only) the opposite one
+#pragma unroll
+        for (int i = 0; i < 9; ++i) g[i * plane] = src[i * plane];
+    }
+}
+
+#ifndef LBM_TB_MIN_BLOCKS
+#define LBM_TB_MIN_BLOCKS 2
+#endif
+
+template <int TM>
+__global__ void __launch_bounds__(kTbThreads, LBM_TB_MIN_BLOCKS)
+    k_batch_tb(const BatchProb* __restrict__ probs, const int4* __restrict__ segs, int nsegs, int nsteps,
+               int ns_max, int rows_max, long long* level_ptr, unsigned* bar_count, unsigned* bar_gen,
+               unsigned* status) {
+    __shared__ Model<float> sM;
+    __shared__ Grid<float> sG;
+    extern __shared__ __align__(16) float tbuf[];
+    const int wb = tb_width(ns_max);
+    const int plane = (rows_max + 2) * wb;
+    const int tid = threadIdx.x;
+    const long long level0 = *(volatile long long*)level_ptr;
+    unsigned bits = 0;
+    const int per = (nsegs + gridDim.x - 1) / gridDim.x;
+    const int g0 = blockIdx.x * per, g1 = min(nsegs, g0 + per);
+    int done = 0;
+    while (done < nsteps) {
+        int n = min(ns_max, nsteps - done);
+        if ((n & 1) == 0) --n;  // odd: level + n lies in the other level buffer
+        const long long level = level0 + done;
+        if (*(volatile unsigned*)status & ST_TIMEOUT) return;
+        int cur = -1;
+        for (int g = g0; g < g1; ++g) {
+            const int4 Sg = segs[g];
+            const BatchProb& P = probs[Sg.x];
+            __syncthreads();  // the previous segment's buffers and constants are no longer read
+            if (Sg.x != cur) {
+                copy_words(reinterpret_cast<float*>(&sM), reinterpret_cast<const float*>(&P.M),
+                           (int)(sizeof(Model<float>) / sizeof(float)));
+                copy_words(reinterpret_cast<int*>(&sG), reinterpret_cast<const int*>(&P.G),
+                           (int)(sizeof(Grid<float>) / sizeof(int)));
+                cur = Sg.x;
+                __syncthreads();
+            }
+            const int nx = sG.nx, ny = sG.ny;
+            const int x0 = Sg.y, xo = x0 - n;  // buffer column 0 is global column xo
+            const size_t pl = (size_t)sG.plane;
+            float* A = tbuf;
+            float* B = tbuf + 9 * plane;
+            // load level `level` over columns [max(xo, -1), min(x0 + kTbW + n, nx + 1)), rows -1 .. ny
+            {
+                const float* fin = P.f[(int)(level & 1)];
+                const int xa = max(xo, -1), xb = min(x0 + kTbW + n, nx + 1);
+                const int w = xb - xa, rows = ny + 2;
+                for (int q = tid; q < 9 * rows * w; q += kTbThreads) {
+                    const int i = q / (rows * w), rem = q % (rows * w);
+                    const int r = rem / w, x = xa + rem % w;
+                    A[i * plane + r * wb + (x - xo)] = __ldcg(fin + i * pl + (size_t)r * sG.pitch + (x + PADX));
+                }
+            }
+            __syncthreads();
+            for (int j = 0; j < n; ++j) {
+                const long long lj = level + j;
+                const int ca = max(x0 - (n - 1 - j), 0), cb = min(x0 + kTbW + (n - 1 - j), nx);
+                const int w = cb - ca;
+                for (int q = tid; q < w * ny; q += kTbThreads) {
+                    const int y = q / w, x = ca + q % w;
+                    const float* c = A + (y + 1) * wb + (x - xo);
+                    float f[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) f[i] = c[i * plane];
+                    float rho, ux, uy, Tt;
+                    moments<float, TM>(f, sM, rho, ux, uy, Tt);
+                    bits |= health(rho, ux, uy, Tt);
+                    float ofe[9];
+                    relaxation<float, TM>(sM, f, rho, ux, uy, Tt, ofe);
+                    float* o = B + (y + 1) * wb + (x - xo);
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        const float* cp = c + i * plane;
+                        o[i * plane] = update(sM, i, ofe[i], f[i], cp[1], cp[-1], cp[wb], cp[-wb]);
+                    }
+                }
+                __syncthreads();
+                // ghost cells of level lj + 1 that the next sub-step or the store reads
+                for (int q = tid; q < 2 * w; q += kTbThreads)
+                    tb_ghost(sG, B, wb, plane, xo, q < w ? S_BOTTOM : S_TOP, ca + (q < w ? q : q - w), lj + 1);
+                if (xo <= -1)
+                    for (int y = tid; y < ny; y += kTbThreads) tb_ghost(sG, B, wb, plane, xo, S_LEFT, y, lj + 1);
+                if (x0 + kTbW + n > nx)
+                    for (int y = tid; y < ny; y += kTbThreads) tb_ghost(sG, B, wb, plane, xo, S_RIGHT, y, lj + 1);
+                __syncthreads();
+                float* t = A;
+                A = B;
+                B = t;
+            }
+            // store level `level + n`: the segment's columns with their ghost rows,
+            // and the ghost columns at the problem's ends
+            {
+                float* fout = P.f[(int)((level + n) & 1)];
+                const int xa = x0 == 0 ? -1 : x0, xb = x0 + kTbW >= nx ? nx + 1 : x0 + kTbW;
+                const int w = xb - xa, rows = ny + 2;
+                for (int q = tid; q < 9 * rows * w; q += kTbThreads) {
+                    const int i = q / (rows * w), rem = q % (rows * w);
+                    const int r = rem / w, x = xa + rem % w;
+                    const bool corner = (x < 0 || x >= nx) && (r == 0 || r == rows - 1);
+                    if (!corner) fout[i * pl + (size_t)r * sG.pitch + (x + PADX)] = A[i * plane + r * wb + (x - xo)];
+                }
+            }
+        }
+        if (!grid_barrier(bar_count, bar_gen, status)) return;
+        done += n;
+    }
+    report(status, bits);
+    if (blockIdx.x == 0 && threadIdx.x == 0) *level_ptr = level0 + nsteps;
+}
+
 }  // namespace
 
 int batch_tile_dims(int* w, int* h) {
@@ -292,5 +454,59 @@ LBM_BATCH_INST(T_INT64)
 LBM_BATCH_INST(T_DF)
 LBM_BATCH_INST(T_CONS)
 #undef LBM_BATCH_INST
+
+size_t batch_tb_smem(int ns, int rows_max) {
+    return sizeof(float) * 2 * 9 * (size_t)(rows_max + 2) * tb_width(ns);
+}
+
+int batch_tb_width() { return kTbW; }
+
+template <int TM>
+cudaError_t launch_batch_tb(const BatchProb* probs, const int4* segs, int nsegs, int nsteps, int ns, int rows_max,
+                            long long* level, unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid,
+                            cudaStream_t st) {
+    auto kern = k_batch_tb<TM>;
+    const size_t smem = batch_tb_smem(ns, rows_max);
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    void* args[] = {(void*)&probs, (void*)&segs,  (void*)&nsegs,     (void*)&nsteps,  (void*)&ns,
+                    (void*)&rows_max, (void*)&level, (void*)&bar_count, (void*)&bar_gen, (void*)&status};
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(grid);
+    cfg.blockDim = dim3(kTbThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelExC(&cfg, (const void*)kern, args);
+}
+
+template <int TM>
+int batch_tb_max_grid(int ns, int rows_max) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const size_t smem = batch_tb_smem(ns, rows_max);
+    if (cudaFuncSetAttribute(k_batch_tb<TM>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_tb<TM>, kTbThreads, smem);
+    return sms * per_sm;
+}
+
+#define LBM_BATCH_TB_INST(TM)                                                                                \
+    template cudaError_t launch_batch_tb<TM>(const BatchProb*, const int4*, int, int, int, int, long long*,  \
+                                             unsigned*, unsigned*, unsigned*, int, cudaStream_t);            \
+    template int batch_tb_max_grid<TM>(int, int);
+LBM_BATCH_TB_INST(T_INT32)
+LBM_BATCH_TB_INST(T_INT64)
+LBM_BATCH_TB_INST(T_DF)
+LBM_BATCH_TB_INST(T_CONS)
+#undef LBM_BATCH_TB_INST
 
 }  // namespace lbm

@@ -100,7 +100,7 @@ cudaError_t launch_feq_vjp(const S* r, const S* ux, const S* uy, const S* T, con
                            S* gy, S* gT, const Model<S>& M, long long n, cudaStream_t st);
 
 // Batch (lbm_batch.cu): FP32 problems advanced by one cooperative launch.
-struct alignas(64) BatchProb {
+struct BatchProb {  // 128-byte aligned by its tensor maps
     CUtensorMap tm[2];  // tensor maps of the two levels (box: batch_box_dims x 9)
     float* f[2];        // the two levels; level k lives in f[k & 1]
     Model<float> M;
@@ -116,6 +116,18 @@ cudaError_t launch_batch(const BatchProb* probs, const int4* tiles, int ntiles, 
                          cudaStream_t st);
 template <int TM>
 int batch_max_grid(int npt);
+// Temporal blocking for thin problems (at most rows_max rows, no periodic x
+// sides): segments of batch_tb_width() columns, ns (odd) steps per pass in
+// shared memory.  segs: (problem, first column, 0, 0).
+constexpr int kBatchTbRowsMax = 8;
+int batch_tb_width();
+size_t batch_tb_smem(int ns, int rows_max);
+template <int TM>
+cudaError_t launch_batch_tb(const BatchProb* probs, const int4* segs, int nsegs, int nsteps, int ns, int rows_max,
+                            long long* level, unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid,
+                            cudaStream_t st);
+template <int TM>
+int batch_tb_max_grid(int ns, int rows_max);
 
 // von Neumann scan (lbm_vonneumann.cu): one case is the step's constants
 // (folded weights, omega, equilibrium coefficients) and a uniform state.

@@ -63,10 +63,10 @@ class lbm_problem(ctypes.Structure):
 
 
 class lbm_batch_launch(ctypes.Structure):
-    _fields_ = [("npt", ctypes.c_int), ("grid", ctypes.c_int)]
+    _fields_ = [("npt", ctypes.c_int), ("grid", ctypes.c_int), ("block", ctypes.c_int)]
 
     def as_tuple(self):
-        return (self.npt, self.grid)
+        return (self.npt, self.grid, self.block)
 
 
 class lbm_vn_case(ctypes.Structure):
@@ -402,8 +402,9 @@ def lbm_batch_problem(b, p):
     return load().lbm_batch_problem(b, int(p))
 
 
-def lbm_batch_set_launch(b, npt, grid=0):
-    return _bcheck(b, load().lbm_batch_set_launch(b, ctypes.byref(lbm_batch_launch(int(npt), int(grid)))))
+def lbm_batch_set_launch(b, npt, grid=0, block=0):
+    l = lbm_batch_launch(int(npt), int(grid), int(block))
+    return _bcheck(b, load().lbm_batch_set_launch(b, ctypes.byref(l)))
 
 
 def lbm_batch_get_launch(b):
@@ -413,9 +414,9 @@ def lbm_batch_get_launch(b):
 
 
 def lbm_batch_autotune(b, steps=10):
-    """Returns ((npt, grid) chosen, per-step ms of each candidate)."""
+    """Returns ((npt, grid, block) chosen, per-step ms of each candidate)."""
     best = lbm_batch_launch()
-    ms = (ctypes.c_double * 4)()
+    ms = (ctypes.c_double * 8)()
     n = ctypes.c_int(0)
     _bcheck(b, load().lbm_batch_autotune(b, int(steps), ctypes.byref(best), ms, ctypes.byref(n)))
     return best.as_tuple(), list(ms[:n.value])
@@ -502,8 +503,8 @@ class Batch:
     def info(self):
         return lbm_batch_info(self.handle)
 
-    def set_launch(self, npt: int, grid: int = 0):
-        lbm_batch_set_launch(self.handle, npt, grid)
+    def set_launch(self, npt: int, grid: int = 0, block: int = 0):
+        lbm_batch_set_launch(self.handle, npt, grid, block)
         return self
 
     def get_launch(self):

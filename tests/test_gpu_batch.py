@@ -62,20 +62,22 @@ def test_batch_argument_errors():
         assert ei.value.status == lbm.LBM_E_STATE
 
 
-@pytest.mark.parametrize("shape", [(2, 0), (1, 7), (2, 3)])
+@pytest.mark.parametrize("shape", [(2, 0, 0), (1, 7, 0), (2, 3, 0), (1, 0, 3), (1, 0, 5), (1, 5, 7)])
 def test_every_batch_launch_shape_gives_the_same_bits(shape):
-    """Two nodes per thread (128-thread CTAs) and grids of a few CTAs walk the
-    same tiles with the same per-node arithmetic: the levels equal those of
-    the default shape (one node per thread, a full wave) bit for bit."""
+    """Two nodes per thread (128-thread CTAs), grids of a few CTAs, and
+    temporal blocking with 3, 5 or 7 steps per pass (120 steps: whole passes
+    and a shorter last one) do the same per-node arithmetic and ghost rules:
+    the levels equal those of the default shape (one node per thread, one
+    step per launch pass, a full wave) bit for bit."""
     probs = _subset()
     fields = [W.initial_fields(p) for p in probs]
     out = {}
-    for sh in [(1, 0), shape]:
+    for sh in [(1, 0, 0), shape]:
         with lbm.Batch(probs, "fp32_cons") as b:
             b.init(fields).set_launch(*sh).step(120)
             b.sync()
             out[sh] = [b.get_f(k).cpu().numpy() for k in range(len(probs))]
-    for a, c in zip(out[(1, 0)], out[shape]):
+    for a, c in zip(out[(1, 0, 0)], out[shape]):
         assert np.array_equal(a, c)
 
 
@@ -84,9 +86,9 @@ def test_batch_autotune_restores_state_and_picks_a_shape():
     fields = [W.initial_fields(p) for p in probs]
     with lbm.Batch(probs, "fp32_cons") as b:
         b.init(fields).step(30)
-        (npt, grid), ms = b.autotune(steps=5)
-        assert len(ms) == 4 and all(m > 0 for m in ms)
-        assert (npt, grid) == b.get_launch() and npt in (1, 2) and grid > 0
+        (npt, grid, block), ms = b.autotune(steps=5)
+        assert len(ms) == 7 and all(m > 0 for m in ms)
+        assert (npt, grid, block) == b.get_launch() and npt in (1, 2) and grid > 0 and block in (0, 3, 5, 7)
         b.step(40)
         b.sync()
         grid_info, _, graph = b.info()
@@ -103,7 +105,12 @@ def test_batch_autotune_restores_state_and_picks_a_shape():
 def test_batch_launch_shape_errors():
     probs = _subset()[:2]
     with lbm.Batch(probs, "fp32") as b:
-        for bad in [(3, 0), (1, -1), (2, 10 ** 6)]:
+        for bad in [(3, 0, 0), (1, -1, 0), (2, 10 ** 6, 0), (1, 0, 4), (1, 10 ** 6, 3)]:
             with pytest.raises(lbm.LbmError) as ei:
                 b.set_launch(*bad)
             assert ei.value.status == lbm.LBM_E_INVAL
+    wide = [W.uniform(70, 12, (1.0, 0.1, 0.0, 1.0), sides=(W.Side("outflow"),) * 4)]
+    with lbm.Batch(wide, "fp32") as b:  # 12 rows: too many for temporal blocking
+        with pytest.raises(lbm.LbmError) as ei:
+            b.set_launch(1, 0, 3)
+        assert ei.value.status == lbm.LBM_E_INVAL
