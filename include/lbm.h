@@ -252,11 +252,11 @@ typedef struct lbm_launch {
                     shared-memory ring by bulk asynchronous copies;
                     2: FP32 modes only: each thread updates tx x-adjacent
                     nodes with vector loads and stores;
-                    3: FP32 modes only (default): persistent CTAs of 64 x 8
-                    threads; each 64 x 8 tile plus its halo (72 x 10 x 9
-                    planes) arrives in shared memory by one tiled tensor copy
-                    (TMA), double-buffered, and the stencil reads shared
-                    memory */
+                    3: FP32 modes only (default): persistent CTAs of 128
+                    threads, two x-adjacent nodes each; each 64 x 4 tile plus
+                    its halo (72 x 6 x 9 planes) arrives in shared memory by
+                    one tiled tensor copy (TMA), double-buffered, and the
+                    stencil reads shared memory */
     int tx;      /* variant 1: columns per CTA, 128 or 256; variant 2: 2 or 4 */
     int ring;    /* variant 1: ring slots, 4 or 6 (4 when tx = 128) */
     int grid;    /* variants 1, 3: CTAs; 0 = one full wave (SMs x resident CTAs) */

@@ -57,18 +57,19 @@ cudaError_t launch_vec(const float* fin, float* fout, const Model<float>& M, con
 }
 
 // ------------------------------------------------------ FP32 TMA tile kernel
-// Persistent CTAs of 32 x 8 threads walk 64 x 8-node tiles.  For each tile
-// one thread issues a single tiled tensor copy of the 72 x 10 x 9 box (4
-// extra columns on each side for 16-byte alignment, one extra row above and
-// below, all nine planes) into one of two shared-memory stages; the next
-// tile's box is in flight while the current one is computed.  Each thread
+// Persistent CTAs of 32 x LBM_TILE_Y threads (default 32 x 4, six CTAs per
+// SM) walk 64 x LBM_TILE_Y-node tiles.  For each tile one thread issues a
+// single tiled tensor copy of the 72 x (LBM_TILE_Y + 2) x 9 box (4 extra
+// columns on each side for 16-byte alignment, one extra row above and below,
+// all nine planes) into one of two shared-memory stages; the next tile's box
+// is in flight while the current one is computed.  Each thread
 // updates two x-adjacent nodes: it reads their values and those of the rows
 // above and below as 8-byte pairs from shared memory, the outer x neighbours
 // as single floats, and writes 8-byte pairs (no global loads, no per-load
 // 64-bit address arithmetic).  Waits are bounded: on give-up the CTA raises
 // ST_TIMEOUT, drains its copies in flight and returns.
 #ifndef LBM_TILE_Y
-#define LBM_TILE_Y 8
+#define LBM_TILE_Y 4
 #endif
 constexpr int kTileX = 64, kTileY = LBM_TILE_Y;
 constexpr int kTileThreads = (kTileX / 2) * kTileY;
@@ -82,7 +83,7 @@ constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages start on 12
 #define LBM_TILE_STAGES 2
 #endif
 #ifndef LBM_TILE_MIN_BLOCKS
-#define LBM_TILE_MIN_BLOCKS 3
+#define LBM_TILE_MIN_BLOCKS 6
 #endif
 constexpr int kStages = LBM_TILE_STAGES;
 static_assert(kStages >= 2 && kStages <= 8, "2 to 8 stages");
