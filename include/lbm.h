@@ -150,7 +150,8 @@ typedef struct lbm_ctx lbm_ctx;
  * with dt equal to the Knudsen number, Sec. 2).  bc[4] in LBM_SIDE_* order.
  * stream: a cudaStream_t (NULL = the legacy default stream) on the current
  * device, which the context keeps using.  Allocates two distribution buffers
- * of 9 x (ny + 2) x pitch elements each (pitch >= nx + 8), owned by the
+ * of (ny + 2) x 9 x pitch elements each (pitch >= nx + 8; internal layout:
+ * row-interleaved, each grid row's nine population rows together), owned by the
  * context.  On failure *out is NULL and lbm_last_error(NULL) explains. */
 lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx,
                       const lbm_dvm* dvm, const lbm_dissipation* diss, const lbm_bc bc[4],
@@ -438,6 +439,19 @@ lbm_status lbm_vn_scan(const lbm_vn_case* cases, int ncases, const int* dirs, in
  * paper: the benchmark's ceiling for the FP64 step, which is bounded by the
  * FP64 pipe rather than by HBM on this part. */
 lbm_status lbm_probe_rates(double* fp64_tflops, double* fp32_tflops);
+
+/* Data-movement ceiling of the FP32 tile step (LBM_STEP_TILE) on an nx x ny
+ * grid: a kernel with the step kernel's tile walk, its tensor copies of the
+ * 72 x 9 x 6 halo boxes of one level and its 8-byte stores of the other
+ * level, but no arithmetic (each node's nine values are copied through).
+ * *gbs = 72 bytes (nine FP32 values read and nine written) per node over
+ * the best of `reps` launches (after two warm-up launches), alternating the
+ * two levels.  Allocates and frees two levels of its own; synchronises.
+ * Not from the paper: the benchmark reports the step kernel against it.
+ * LBM_E_INVAL for nx, ny < 1, reps < 1 or gbs NULL; LBM_E_NOMEM; LBM_E_CUDA
+ * (also when the tensor-copy interface is unavailable); LBM_E_TIMEOUT if a
+ * bounded wait of the kernel gave up. */
+lbm_status lbm_probe_tile_copy(int nx, int ny, int reps, double* gbs);
 
 /* Version string of the library. */
 const char* lbm_version(void);

@@ -83,15 +83,15 @@ __device__ __forceinline__ void write_periodic_ghosts(const Grid<S>& G, S* __res
     const size_t pl = (size_t)G.plane;
     if (G.kind_lo[S_LEFT] == BC_PERIODIC) {
         if (ix == G.nx - 1)
-            for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(iy + 1) * G.pitch + (PADX - 1)] = v[i];
+            for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(iy + 1) * G.row + (PADX - 1)] = v[i];
         if (ix == 0)
-            for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(iy + 1) * G.pitch + (PADX + G.nx)] = v[i];
+            for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(iy + 1) * G.row + (PADX + G.nx)] = v[i];
     }
     if (G.kind_lo[S_BOTTOM] == BC_PERIODIC) {
         if (iy == G.ny - 1)
             for (int i = 0; i < 9; ++i) a[i * pl + (size_t)ix + PADX] = v[i];
         if (iy == 0)
-            for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(G.ny + 1) * G.pitch + ix + PADX] = v[i];
+            for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(G.ny + 1) * G.row + ix + PADX] = v[i];
     }
 }
 
@@ -218,9 +218,9 @@ __global__ void __launch_bounds__(kAdjThreads, 3)
         float* dst = stage0 + st * kAdjStageFloats;
         mbar_arrive_expect_tx(&bar[st], (uint32_t)(sizeof(float) * (kAdjAFloats + kAdjFFloats)));
         // adjoint box: array column x0 = interior x0 - 4, array row y0 = interior y0 - 1
-        tma_load_3d(dst, &tmapA, x0, y0, 0, &bar[st]);
+        tma_load_3d(dst, &tmapA, x0, 0, y0, &bar[st]);
         // f box: the tile itself (array column x0 + 4, row y0 + 1)
-        tma_load_3d(dst + kAdjAPad, &tmapF, x0 + PADX, y0 + 1, 0, &bar[st]);
+        tma_load_3d(dst + kAdjAPad, &tmapF, x0 + PADX, 0, y0 + 1, &bar[st]);
     };
     auto wait = [&](int k) { return mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), kAdjWaitLimit); };
     int issued = -1, waited = -1;
@@ -229,7 +229,9 @@ __global__ void __launch_bounds__(kAdjThreads, 3)
         issued = 0;
     }
     const size_t pl = (size_t)G.plane;
-    constexpr int PA = kAdjBoxX * kAdjBoxY, PF = kAdjTX * kAdjTY;
+    // boxes in shared memory are [row][population][column], like the levels:
+    // population strides PA, PF and row strides RA, RF
+    constexpr int PA = kAdjBoxX, RA = 9 * kAdjBoxX, PF = kAdjTX, RF = 9 * kAdjTX;
     float wsum = 0.0f;  // this warp's tau terms, tile by tile in a fixed order (FP32 over a few tiles)
     for (int k = 0;; ++k) {
         const int t = blockIdx.x + k * gridDim.x;
@@ -249,8 +251,8 @@ __global__ void __launch_bounds__(kAdjThreads, 3)
         const int ix = (t % tiles_x) * kAdjTX + tx, iy = (t / tiles_x) * kAdjTY + ty;
         float tn = 0.0f;
         if (ix < G.nx && iy < G.ny) {
-            const float* sA = stage0 + (k & 1) * kAdjStageFloats + (ty + 1) * kAdjBoxX + (tx + 4);
-            const float* sF = stage0 + (k & 1) * kAdjStageFloats + kAdjAPad + ty * kAdjTX + tx;
+            const float* sA = stage0 + (k & 1) * kAdjStageFloats + (ty + 1) * RA + (tx + 4);
+            const float* sF = stage0 + (k & 1) * kAdjStageFloats + kAdjAPad + ty * RF + tx;
             // the box holds the star of every node: interior neighbours, the
             // wrapped values in the ghost cells of periodic sides, zeros in
             // the ghost cells of the others
@@ -262,8 +264,8 @@ __global__ void __launch_bounds__(kAdjThreads, 3)
                 av[i] = pA[0];
                 aL[i] = pA[-1];
                 aR[i] = pA[1];
-                aD[i] = pA[-kAdjBoxX];
-                aU[i] = pA[kAdjBoxX];
+                aD[i] = pA[-RA];
+                aU[i] = pA[RA];
             }
             adjoint_core<float, TM>(M, fv, av, aL, aR, aD, aU, o, tn);
             const size_t c = cell(G, ix, iy);

@@ -18,7 +18,7 @@ using namespace lbm;
 struct lbm_ctx {
     int device = 0;
     int nx = 0, ny = 0, pitch = 0;
-    long long plane = 0;
+    long long plane = 0, row = 0;  // population and row strides of a level (elements)
     lbm_precision prec = LBM_FP64;
     size_t esize = 8;
     double b = 0, tau = 0, dt = 0, dx = 0;
@@ -210,6 +210,7 @@ Grid<S> build_grid(const lbm_ctx& c, const Model<double>& M) {
     G.ny = c.ny;
     G.pitch = c.pitch;
     G.plane = c.plane;
+    G.row = c.row;
     G.dt = c.dt;
     G.dx = c.dx;
     for (int s = 0; s < 4; ++s) {
@@ -350,7 +351,7 @@ lbm_status device_view(lbm_ctx* c, const void* p, size_t bytes, size_t offset, c
     return LBM_OK;
 }
 
-size_t level_bytes(const lbm_ctx* c) { return (size_t)9 * (size_t)c->plane * c->esize; }
+size_t level_bytes(const lbm_ctx* c) { return (size_t)(c->ny + 2) * (size_t)c->row * c->esize; }
 
 // Keep a copy of the current level (padded, ghosts included) as checkpoint k.
 lbm_status save_checkpoint(lbm_ctx* c, size_t k) {
@@ -396,14 +397,15 @@ EncodeTiledFn encode_fn() {
     return fn;
 }
 
-// 3D map (x: pitch columns, y: ny + 2 rows, z: 9 planes) of one FP32 level
-// with a bx x by x 9 box.
+// 3D map (x: pitch columns, y: the 9 populations, z: ny + 2 rows) of one
+// FP32 level in its row-interleaved layout, with a bx x 9 x by box (in
+// shared memory: [row][population][column]).
 bool make_tmap_box(CUtensorMap* m, void* base, const lbm_ctx& c, int bx, int by) {
     EncodeTiledFn fn = encode_fn();
     if (!fn) return false;
-    const cuuint64_t dims[3] = {(cuuint64_t)c.pitch, (cuuint64_t)(c.ny + 2), 9};
-    const cuuint64_t strides[2] = {(cuuint64_t)c.pitch * 4, (cuuint64_t)c.plane * 4};
-    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 9};
+    const cuuint64_t dims[3] = {(cuuint64_t)c.pitch, 9, (cuuint64_t)(c.ny + 2)};
+    const cuuint64_t strides[2] = {(cuuint64_t)c.plane * 4, (cuuint64_t)c.row * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, 9, (cuuint32_t)by};
     const cuuint32_t es[3] = {1, 1, 1};
     return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, base, dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -417,6 +419,7 @@ bool make_tmap(CUtensorMap* m, void* base, const lbm_ctx& c) {
     return make_tmap_box(m, base, c, bx, by);
 }
 
+
 struct CkptHeader {
     char magic[8];
     int nx, ny, prec, esize;
@@ -427,6 +430,69 @@ struct CkptHeader {
 static_assert(sizeof(CkptHeader) == 64, "checkpoint header is 64 bytes");
 
 }  // namespace
+
+extern "C" lbm_status lbm_probe_tile_copy(int nx, int ny, int reps, double* gbs) {
+    if (nx < 1 || ny < 1 || reps < 1 || !gbs) return LBM_E_INVAL;
+    lbm_ctx c;  // layout fields only
+    c.nx = nx;
+    c.ny = ny;
+    c.pitch = ((nx + 2 * PADX) + 31) / 32 * 32;
+    c.plane = c.pitch;
+    c.row = 9LL * c.pitch;
+    c.esize = 4;
+    const size_t bytes = level_bytes(&c);
+    Grid<float> G{};
+    G.nx = nx;
+    G.ny = ny;
+    G.pitch = c.pitch;
+    G.plane = c.plane;
+    G.row = c.row;
+    void* f[2] = {nullptr, nullptr};
+    unsigned* status = nullptr;
+    cudaStream_t st = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    lbm_status r = LBM_OK;
+    CUtensorMap m[2];
+    if (cudaMalloc(&f[0], bytes) != cudaSuccess || cudaMalloc(&f[1], bytes) != cudaSuccess ||
+        cudaMalloc((void**)&status, sizeof(unsigned)) != cudaSuccess) {
+        r = LBM_E_NOMEM;
+    } else if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
+               cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
+               cudaMemsetAsync(f[0], 0, bytes, st) != cudaSuccess ||
+               cudaMemsetAsync(f[1], 0, bytes, st) != cudaSuccess ||
+               cudaMemsetAsync(status, 0, sizeof(unsigned), st) != cudaSuccess) {
+        r = LBM_E_CUDA;
+    } else if (!make_tmap(&m[0], f[0], c) || !make_tmap(&m[1], f[1], c)) {
+        r = LBM_E_CUDA;
+    } else {
+        float best = 1e30f;
+        for (int k = 0; k < reps + 2 && r == LBM_OK; ++k) {
+            const int a = k & 1;
+            if (cudaEventRecord(e0, st) != cudaSuccess ||
+                launch_tile_copy(m[a], static_cast<float*>(f[a ^ 1]), G, status, st) != cudaSuccess ||
+                cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                r = LBM_E_CUDA;
+                break;
+            }
+            float ms = 0.0f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (k >= 2 && ms < best) best = ms;
+        }
+        unsigned h = 0;
+        if (r == LBM_OK && cudaMemcpy(&h, status, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess)
+            r = LBM_E_CUDA;
+        if (r == LBM_OK && (h & ST_TIMEOUT)) r = LBM_E_TIMEOUT;
+        if (r == LBM_OK) *gbs = 72.0 * (double)nx * (double)ny / (best * 1e-3) / 1e9;
+    }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+    if (st) cudaStreamDestroy(st);
+    cudaFree(f[0]);
+    cudaFree(f[1]);
+    cudaFree(status);
+    cudaGetLastError();
+    return r;
+}
 
 extern "C" {
 
@@ -452,7 +518,8 @@ lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx
     c->nx = nx;
     c->ny = ny;
     c->pitch = ((nx + 2 * PADX) + 31) / 32 * 32;
-    c->plane = (long long)(ny + 2) * c->pitch;
+    c->plane = c->pitch;
+    c->row = 9LL * c->pitch;
     c->prec = prec;
     c->esize = prec == LBM_FP64 ? 8 : 4;
     c->b = b;
@@ -468,7 +535,7 @@ lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx
     c->mf = cast_model<float>(c->md);
     c->gd = build_grid<double>(*c, c->md);
     c->gf = build_grid<float>(*c, c->md);
-    const size_t fbytes = (size_t)9 * (size_t)c->plane * c->esize;
+    const size_t fbytes = level_bytes(c);
     cudaError_t e = cudaSuccess;
     for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&c->f[k], fbytes);
     if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_status, sizeof(unsigned));

@@ -66,8 +66,9 @@ __device__ __forceinline__ void copy_words(S* dst, const S* src, int n) {
 
 constexpr int kBoxW = kTileW + 8;  // 4 extra columns each side keep 16-byte alignment
 constexpr int kBoxH = kTileH + 2;
-constexpr int kBoxPlane = kBoxW * kBoxH;
-constexpr int kBoxFloats = 9 * kBoxPlane;
+// The box in shared memory is [row][population][column], like the level.
+constexpr int kBoxPop = kBoxW, kBoxRow = 9 * kBoxW;  // population and row strides
+constexpr int kBoxFloats = kBoxH * kBoxRow;
 constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages on 128-byte boundaries
 constexpr size_t kBatchSmem = 128 + sizeof(float) * 2 * kStageFloats + 2 * sizeof(uint64_t);
 
@@ -104,7 +105,7 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
         const int4 T = tiles[t];
         mbar_arrive_expect_tx(&bar[k & 1], (uint32_t)(sizeof(float) * kBoxFloats));
         // array column T.y (interior column T.y - 4), array row T.z (interior row T.z - 1)
-        tma_load_3d(box0 + (k & 1) * kStageFloats, &probs[T.x].tm[par], T.y, T.z, 0, &bar[k & 1]);
+        tma_load_3d(box0 + (k & 1) * kStageFloats, &probs[T.x].tm[par], T.y, 0, T.z, &bar[k & 1]);
     };
     auto wait = [&](int k) { return mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), kBatchWaitLimit); };
     int k = 0, issued = -1, waited = -1;
@@ -145,10 +146,10 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
             if constexpr (NPT == 1) {
                 const int ix = T.y + cx, iy = T.z + r;
                 if (ix < sG.nx && iy < sG.ny) {
-                    const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxW + (cx + 4);
+                    const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxRow + (cx + 4);
                     float f[9];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) f[i] = b[i * kBoxPlane];
+                    for (int i = 0; i < 9; ++i) f[i] = b[i * kBoxPop];
                     float rho, ux, uy, Tt;
                     moments<float, TM>(f, sM, rho, ux, uy, Tt);
                     bits |= health(rho, ux, uy, Tt);
@@ -156,8 +157,8 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
                     relaxation<float, TM>(sM, f, rho, ux, uy, Tt, ofe);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        const float* bp = b + i * kBoxPlane;
-                        o[i] = update(sM, i, ofe[i], f[i], bp[1], bp[-1], bp[kBoxW], bp[-kBoxW]);
+                        const float* bp = b + i * kBoxPop;
+                        o[i] = update(sM, i, ofe[i], f[i], bp[1], bp[-1], bp[kBoxRow], bp[-kBoxRow]);
                     }
                     float* fout = P.f[par ^ 1];
                     const size_t pl = (size_t)sG.plane;
@@ -171,10 +172,10 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
                 const int ix0 = T.y + 2 * cx, iy = T.z + r;
                 if (ix0 < sG.nx && iy < sG.ny) {
                     const int nvalid = min(2, sG.nx - ix0);
-                    const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxW + (2 * cx + 4);
+                    const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxRow + (2 * cx + 4);
                     float2 C[9];
 #pragma unroll
-                    for (int i = 0; i < 9; ++i) C[i] = *reinterpret_cast<const float2*>(b + i * kBoxPlane);
+                    for (int i = 0; i < 9; ++i) C[i] = *reinterpret_cast<const float2*>(b + i * kBoxPop);
                     float acc[9][2];
 #pragma unroll
                     for (int j = 0; j < 2; ++j) {
@@ -194,9 +195,9 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
                     float* out = fout + cell(sG, ix0, iy);  // 8-byte aligned: ix0 + PADX is even
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        const float* bp = b + i * kBoxPlane;
-                        const float2 Nn = *reinterpret_cast<const float2*>(bp + kBoxW);
-                        const float2 Ss = *reinterpret_cast<const float2*>(bp - kBoxW);
+                        const float* bp = b + i * kBoxPop;
+                        const float2 Nn = *reinterpret_cast<const float2*>(bp + kBoxRow);
+                        const float2 Ss = *reinterpret_cast<const float2*>(bp - kBoxRow);
                         const float Wv = bp[-1], Ev = bp[2];
                         float2 o;
                         o.x = update(sM, i, acc[i][0], C[i].x, C[i].y, Wv, Nn.x, Ss.x);
@@ -327,7 +328,7 @@ __global__ void __launch_bounds__(kTbThreads, LBM_TB_MIN_BLOCKS)
                 for (int q = tid; q < 9 * rows * w; q += kTbThreads) {
                     const int i = q / (rows * w), rem = q % (rows * w);
                     const int r = rem / w, x = xa + rem % w;
-                    A[i * plane + r * wb + (x - xo)] = __ldcg(fin + i * pl + (size_t)r * sG.pitch + (x + PADX));
+                    A[i * plane + r * wb + (x - xo)] = __ldcg(fin + i * pl + (size_t)r * sG.row + (x + PADX));
                 }
             }
             __syncthreads();
@@ -376,7 +377,7 @@ __global__ void __launch_bounds__(kTbThreads, LBM_TB_MIN_BLOCKS)
                     const int i = q / (rows * w), rem = q % (rows * w);
                     const int r = rem / w, x = xa + rem % w;
                     const bool corner = (x < 0 || x >= nx) && (r == 0 || r == rows - 1);
-                    if (!corner) fout[i * pl + (size_t)r * sG.pitch + (x + PADX)] = A[i * plane + r * wb + (x - xo)];
+                    if (!corner) fout[i * pl + (size_t)r * sG.row + (x + PADX)] = A[i * plane + r * wb + (x - xo)];
                 }
             }
         }

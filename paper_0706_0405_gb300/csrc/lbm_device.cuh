@@ -9,9 +9,15 @@
 
 namespace lbm {
 
-// Interior column 0 sits at array column PADX, so that interior rows start on
-// a 32-byte boundary for FP64 and FP32 alike; the ghost columns are PADX - 1
-// and PADX + nx.  Rows 0 and ny + 1 are the ghost rows.
+// Layout of one level in HBM: row-interleaved, [row][population][column].
+// Each of the ny + 2 rows (rows 0 and ny + 1 are the ghost rows) holds the
+// nine population rows of that grid row one after the other, each `pitch`
+// elements long, so a node's nine values are `pitch` apart (Grid::plane) and
+// consecutive grid rows 9 * pitch apart (Grid::row).  A tile of a few rows
+// then lies in a few contiguous runs of HBM rather than 9 far-apart ones per
+// row.  Interior column 0 sits at column PADX, so that interior row segments
+// start on a 32-byte boundary for FP64 and FP32 alike; the ghost columns are
+// PADX - 1 and PADX + nx.
 constexpr int PADX = 4;
 
 // Temperature recovery variants of the FP32 modes (see lbm.h).
@@ -66,8 +72,9 @@ struct Model {
 // Grid and boundary description.
 template <typename S>
 struct Grid {
-    int nx, ny, pitch;
-    long long plane;              // elements per population plane = (ny + 2) * pitch
+    int nx, ny, pitch;            // pitch: elements per population row (>= nx + 2 PADX)
+    long long plane;              // stride between populations of a node = pitch
+    long long row;                // stride between consecutive grid rows = 9 * pitch
     int kind_lo[4], kind_hi[4];
     int split_moving[4];          // 1 if split_speed != 0
     int split_index[4];           // fixed splits: first along-index in the "hi" part
@@ -305,7 +312,7 @@ __device__ __forceinline__ int side_part(const Grid<S>& G, int side, int along_i
 
 template <typename S>
 __device__ __forceinline__ size_t cell(const Grid<S>& G, int ix, int iy) {
-    return (size_t)(iy + 1) * (size_t)G.pitch + (size_t)(ix + PADX);
+    return (size_t)(iy + 1) * (size_t)G.row + (size_t)(ix + PADX);
 }
 
 // Write the ghost cells of level `level` that the edge node (ix, iy), whose
@@ -323,7 +330,7 @@ __device__ __forceinline__ void write_ghosts(const Grid<S>& G, S* __restrict__ f
             const int kind = part ? G.kind_hi[side] : G.kind_lo[side];
             const int own = side == S_LEFT ? 0 : G.nx - 1;
             const int far = side == S_LEFT ? G.nx - 1 : 0;
-            const size_t gc = (size_t)(iy + 1) * G.pitch + (side == S_LEFT ? PADX - 1 : PADX + G.nx);
+            const size_t gc = (size_t)(iy + 1) * G.row + (side == S_LEFT ? PADX - 1 : PADX + G.nx);
             if (kind == BC_PERIODIC) {
                 if (ix == far)
                     for (int i = 0; i < 9; ++i) f[i * pl + gc] = v[i];
@@ -344,7 +351,7 @@ __device__ __forceinline__ void write_ghosts(const Grid<S>& G, S* __restrict__ f
             const int kind = part ? G.kind_hi[side] : G.kind_lo[side];
             const int own = side == S_BOTTOM ? 0 : G.ny - 1;
             const int far = side == S_BOTTOM ? G.ny - 1 : 0;
-            const size_t gc = (size_t)(side == S_BOTTOM ? 0 : G.ny + 1) * G.pitch + (ix + PADX);
+            const size_t gc = (size_t)(side == S_BOTTOM ? 0 : G.ny + 1) * G.row + (ix + PADX);
             if (kind == BC_PERIODIC) {
                 if (iy == far)
                     for (int i = 0; i < 9; ++i) f[i * pl + gc] = v[i];
@@ -409,7 +416,7 @@ __device__ __forceinline__ unsigned node_step(const S* __restrict__ fin, S* __re
     for (int i = 0; i < 9; ++i) {
         const S* p = fin + i * pl + c;
         o[i] = update(M, i, ofe[i], f[i], load_s<S, kCoherent>(p + 1), load_s<S, kCoherent>(p - 1),
-                      load_s<S, kCoherent>(p + G.pitch), load_s<S, kCoherent>(p - G.pitch));
+                      load_s<S, kCoherent>(p + G.row), load_s<S, kCoherent>(p - G.row));
     }
 #pragma unroll
     for (int i = 0; i < 9; ++i) fout[i * pl + c] = o[i];
@@ -507,8 +514,8 @@ __device__ __forceinline__ unsigned vec_group(const float* __restrict__ fin, flo
     for (int i = 0; i < 9; ++i) {
         const float* p = in + i * pl;
         float Nn[V], Ss[V];
-        load_vec<V, kCoherent>(p + G.pitch, Nn);
-        load_vec<V, kCoherent>(p - G.pitch, Ss);
+        load_vec<V, kCoherent>(p + G.row, Nn);
+        load_vec<V, kCoherent>(p - G.row, Ss);
         float row[V + 2];
         row[0] = load1<kCoherent>(p - 1);
         row[V + 1] = load1<kCoherent>(p + V);

@@ -37,6 +37,11 @@ struct StepConfig {
 // Box of the tiled tensor copy of the tile kernel (x, y extent; 9 planes).
 void tile_box_dims(int* bx, int* by);
 
+// The step kernel's data movement alone (lbm_probe_tile_copy): level in the
+// tensor map -> fout, each node's nine values copied through, no ghosts.
+cudaError_t launch_tile_copy(const CUtensorMap& tmap, float* fout, const Grid<float>& G, unsigned* status,
+                             cudaStream_t st);
+
 // One step, level `level` in fin -> level + 1 in fout (ghosts included).
 template <typename S, int TM>
 cudaError_t launch_step(const S* fin, S* fout, const Model<S>& M, const Grid<S>& G,

@@ -110,7 +110,7 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
         const int x0 = (tile % tiles_x) * kTileX, y0 = (tile / tiles_x) * kTileY;
         mbar_arrive_expect_tx(&bar[stage], (uint32_t)(sizeof(float) * kBoxFloats));
         // array column x0 is interior column x0 - 4; array row y0 is interior row y0 - 1
-        tma_load_3d(box + stage * kStageFloats, &tmap, x0, y0, 0, &bar[stage]);
+        tma_load_3d(box + stage * kStageFloats, &tmap, x0, 0, y0, &bar[stage]);
     };
     // local tile k of this CTA lives in stage k % kStages; its phase parity
     // is (k / kStages) & 1
@@ -125,7 +125,8 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
         issued = j;
     }
     const size_t pl = (size_t)G.plane;
-    constexpr int P = kBoxX * kBoxY;  // floats per plane in the box
+    // the box in shared memory is [row][population][column], like the level
+    constexpr int P = kBoxX, R = 9 * kBoxX;  // population and row strides in the box
     unsigned bits = 0;
     for (int k = 0;; ++k) {
         const int t = blockIdx.x + k * gridDim.x;
@@ -152,7 +153,7 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
         if (ix0 >= G.nx || iy >= G.ny) continue;
         const int nvalid = min(2, G.nx - ix0);
         // centre of node ix0 in the box: row ty + 1, column 2 tx + 4 (8-byte aligned)
-        const float* b = box + (k % kStages) * kStageFloats + (ty + 1) * kBoxX + (2 * tx + 4);
+        const float* b = box + (k % kStages) * kStageFloats + (ty + 1) * R + (2 * tx + 4);
         float2 C[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) C[i] = *reinterpret_cast<const float2*>(b + i * P);
@@ -175,8 +176,8 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const float* bp = b + i * P;
-            const float2 Nn = *reinterpret_cast<const float2*>(bp + kBoxX);
-            const float2 Ss = *reinterpret_cast<const float2*>(bp - kBoxX);
+            const float2 Nn = *reinterpret_cast<const float2*>(bp + R);
+            const float2 Ss = *reinterpret_cast<const float2*>(bp - R);
             const float Wv = bp[-1], Ev = bp[2];
             float2 o;
             o.x = update(M, i, acc[i][0], C[i].x, C[i].y, Wv, Nn.x, Ss.x);
@@ -200,6 +201,89 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
         }
     }
     report(status, bits);
+}
+
+// Data-movement twin of k_step_tile for lbm_probe_tile_copy: the same tile
+// walk, the same tensor copies of the halo boxes of one level and the same
+// 8-byte stores of the other, no arithmetic (each node's nine values are
+// copied through).  Its time is what moving the step kernel's bytes costs
+// in this access pattern.
+__global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
+    k_tile_copy(const __grid_constant__ CUtensorMap tmap, float* __restrict__ fout, const Grid<float> G,
+                unsigned* status, int tiles_x, int ntiles) {
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
+    float* box = reinterpret_cast<float*>(smem);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(float) * kStages * kStageFloats);
+    __shared__ int abort_flag;
+    const int tid = threadIdx.x, tx = tid % (kTileX / 2), ty = tid / (kTileX / 2);
+    if (tid == 0) {
+        for (int j = 0; j < kStages; ++j) mbar_init(&bar[j], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+    }
+    __syncthreads();
+    auto issue = [&](int tile, int stage) {
+        mbar_arrive_expect_tx(&bar[stage], (uint32_t)(sizeof(float) * kBoxFloats));
+        tma_load_3d(box + stage * kStageFloats, &tmap, (tile % tiles_x) * kTileX, 0, (tile / tiles_x) * kTileY,
+                    &bar[stage]);
+    };
+    auto wait = [&](int k) {
+        return mbar_wait_bounded(&bar[k % kStages], (uint32_t)((k / kStages) & 1), kWaitLimit);
+    };
+    int issued = -1, waited = -1;
+    for (int j = 0; j < kStages - 1; ++j) {
+        const int t = blockIdx.x + j * gridDim.x;
+        if (t >= ntiles) break;
+        if (tid == 0) issue(t, j);
+        issued = j;
+    }
+    const size_t pl = (size_t)G.plane;
+    for (int k = 0;; ++k) {
+        const int t = blockIdx.x + k * gridDim.x;
+        if (t >= ntiles) break;
+        if (tid == 0 && !wait(k)) abort_flag = 1;
+        __syncthreads();
+        if (abort_flag) {
+            for (int j = waited + 1; j <= issued; ++j) wait(j);
+            if (tid == 0) atomicOr(status, ST_TIMEOUT);
+            return;
+        }
+        waited = k;
+        const int kn = k + kStages - 1, tn = blockIdx.x + kn * gridDim.x;
+        if (tn < ntiles) {
+            if (tid == 0) issue(tn, kn % kStages);
+            issued = kn;
+        }
+        const int ix0 = (t % tiles_x) * kTileX + 2 * tx, iy = (t / tiles_x) * kTileY + ty;
+        if (ix0 >= G.nx || iy >= G.ny) continue;
+        const float* b = box + (k % kStages) * kStageFloats + (ty + 1) * (9 * kBoxX) + (2 * tx + 4);
+        float* out = fout + cell(G, ix0, iy);
+        if (ix0 + 1 < G.nx) {
+#pragma unroll
+            for (int i = 0; i < 9; ++i)
+                *reinterpret_cast<float2*>(out + i * pl) = *reinterpret_cast<const float2*>(b + i * kBoxX);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 9; ++i) out[i * pl] = b[i * kBoxX];
+        }
+    }
+}
+
+cudaError_t launch_tile_copy(const CUtensorMap& tmap, float* fout, const Grid<float>& G, unsigned* status,
+                             cudaStream_t st) {
+    constexpr size_t smem = kTileSmem;
+    cudaError_t e = allow_smem<k_tile_copy>(smem);
+    if (e != cudaSuccess) return e;
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_copy, kTileThreads, smem);
+    const int tiles_x = (G.nx + kTileX - 1) / kTileX;
+    const int ntiles = tiles_x * ((G.ny + kTileY - 1) / kTileY);
+    const int grid = min(ntiles, sms * (per_sm > 0 ? per_sm : 1));
+    k_tile_copy<<<grid, kTileThreads, smem, st>>>(tmap, fout, G, status, tiles_x, ntiles);
+    return cudaGetLastError();
 }
 
 void tile_box_dims(int* bx, int* by) {
@@ -281,7 +365,7 @@ __global__ void __launch_bounds__(TX, 2)
             const long long q = L + k;
             const int slot = (int)(q % R);
             mbar_arrive_expect_tx(&bar[slot], 9u * bytes);
-            const float* src = fin + (size_t)(y0 + k) * G.pitch + x0;
+            const float* src = fin + (size_t)(y0 + k) * G.row + x0;
             float* dst = ring + (size_t)slot * 9 * WPAD;
 #pragma unroll
             for (int i = 0; i < 9; ++i) bulk_g2s(dst + i * WPAD, src + i * pl, bytes, &bar[slot]);

@@ -125,3 +125,12 @@ def test_vn_scan_rejects_invalid_arguments(kw, msg):
 
 def test_vn_scan_with_no_cases_does_nothing():
     lbm.lbm_vn_scan([], [(1, 0)], 31)
+
+
+@pytest.mark.parametrize("args", [(0, 8, 1), (8, 0, 1), (8, 8, 0)])
+def test_probe_tile_copy_rejects_invalid_arguments(args):
+    import ctypes
+    g = ctypes.c_double(-1.0)
+    assert lbm.load().lbm_probe_tile_copy(*args, ctypes.byref(g)) == lbm.LBM_E_INVAL
+    assert lbm.load().lbm_probe_tile_copy(8, 8, 1, None) == lbm.LBM_E_INVAL
+    assert g.value == -1.0

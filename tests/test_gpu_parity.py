@@ -353,3 +353,12 @@ def test_autotune_restores_state_and_picks_a_shape():
     with lbm.Lattice(p, "fp64") as lat:
         with pytest.raises(lbm.LbmError):
             lbm.lbm_set_launch(lat.ctx, 1, 256, 4, 0)
+
+
+def test_probe_tile_copy_measures_a_plausible_bandwidth():
+    """The step kernel's data movement alone on the 4096 x 1024 grid and on a
+    ragged one: a finite positive rate, below twice the device's nominal HBM
+    bandwidth (it moves 72 bytes per node between HBM and the SMs)."""
+    for nx, ny in ((4096, 1024), (333, 77)):
+        g = lbm.lbm_probe_tile_copy(nx, ny, 3)
+        assert np.isfinite(g) and 0.0 < g < 16000.0, (nx, ny, g)
