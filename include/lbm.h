@@ -386,6 +386,29 @@ lbm_status lbm_batch_get_launch(const lbm_batch* batch, lbm_batch_launch* launch
 lbm_status lbm_batch_autotune(lbm_batch* batch, int steps, lbm_batch_launch* best, double* ms,
                               int* n_candidates);
 
+/* Step ordering inside the one-step tile kernel: a CTA starts step s + 1 as
+ * soon as every CTA owning a tile next to one of its own (periodic partners
+ * included) has finished step s, rather than at a grid-wide barrier; one
+ * grid barrier ends each launch.  (A grid barrier after every step remains
+ * for launch shapes whose neighbour lists would be longer than 8 CTAs.)
+ * Every such wait, like the grid barriers, gives up after a bound: the
+ * launch then stops, and the next lbm_batch_sync returns LBM_E_TIMEOUT;
+ * lbm_batch_init makes the batch usable again.
+ *
+ * lbm_batch_set_wait_limit: that bound in seconds, (0, 60], for every batch
+ * of the current device (default 2 s); converted to SM cycles at the
+ * device's nominal clock.  LBM_E_INVAL outside the range.
+ *
+ * lbm_batch_plant_stall: failure injection for tests, on the host side.
+ * cta in [0, grid) adds to that CTA's neighbour list a counter that no CTA
+ * ever advances, so its wait before its second step of the next launch runs
+ * out (after the bound above) and the launch reports LBM_E_TIMEOUT; nothing
+ * faults or hangs.  cta < 0 restores the lists.  LBM_E_STATE if the current
+ * launch shape has no neighbour lists (temporal blocking, or lists too long);
+ * LBM_E_INVAL for cta >= grid.  Synchronises the batch's stream. */
+lbm_status lbm_batch_set_wait_limit(double seconds);
+lbm_status lbm_batch_plant_stall(lbm_batch* batch, int cta);
+
 /* -------------------------------------------------- von Neumann scanner
  * Linear stability of the scheme about a uniform state (Sec. 3): a Fourier
  * mode exp(i k.x) of a perturbation of f is multiplied each step by the 9 x 9

@@ -1134,6 +1134,16 @@ struct lbm_batch {
     BatchProb* d_probs = nullptr;
     int4* d_tiles = nullptr;
     int ntiles = 0;
+    std::vector<int4> tiles;           // host copy of the tile list
+    std::vector<int> tiles_x, tiles_y, tile_base;   // per problem
+    std::vector<char> periodic_x, periodic_y;       // per problem (any part of a side)
+    // step ordering of the tile kernel: neighbour lists for grid nbr_grid
+    int* d_nbr = nullptr;
+    unsigned long long* d_done = nullptr;
+    unsigned long long* d_epoch = nullptr;
+    int nbr_cap = 0;    // CTAs the arrays hold
+    int nbr_grid = -1;  // grid the lists were made for
+    bool nbr_ok = false;
     long long* d_level = nullptr;
     unsigned* d_bar = nullptr;     // [0] arrivals, [1] generation
     unsigned* d_status = nullptr;
@@ -1165,14 +1175,70 @@ lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& msg) {
     return s;
 }
 
+// For each CTA of a grid (CTA c walks tiles [c per, (c + 1) per)), the
+// other CTAs owning a tile next to one of its tiles in x or y, across
+// periodic sides too.  False if some CTA has more than kBatchMaxNbr.
+bool batch_neighbour_lists(const lbm_batch* b, int grid, std::vector<int>& out) {
+    const int per = (b->ntiles + grid - 1) / grid;
+    out.assign((size_t)grid * kBatchMaxNbr, -1);
+    std::vector<int> cnt(grid, 0);
+    auto add = [&](int c, int n) {
+        if (n == c) return true;
+        for (int j = 0; j < cnt[c]; ++j)
+            if (out[(size_t)c * kBatchMaxNbr + j] == n) return true;
+        if (cnt[c] == kBatchMaxNbr) return false;
+        out[(size_t)c * kBatchMaxNbr + cnt[c]++] = n;
+        return true;
+    };
+    int tw = 0, th = 0;
+    batch_tile_dims(&tw, &th);
+    for (int t = 0; t < b->ntiles; ++t) {
+        const int4 T = b->tiles[t];
+        const int p = T.x, tx = b->tiles_x[p], ty = b->tiles_y[p];
+        const int ix = T.y / tw, iy = T.z / th, c = t / per;
+        const int nb[4][2] = {{ix - 1, iy}, {ix + 1, iy}, {ix, iy - 1}, {ix, iy + 1}};
+        for (const auto& q : nb) {
+            int jx = q[0], jy = q[1];
+            if (jx < 0 || jx >= tx) {
+                if (!b->periodic_x[p]) continue;
+                jx = (jx + tx) % tx;
+            }
+            if (jy < 0 || jy >= ty) {
+                if (!b->periodic_y[p]) continue;
+                jy = (jy + ty) % ty;
+            }
+            if (!add(c, (b->tile_base[p] + jy * tx + jx) / per)) return false;
+        }
+    }
+    return true;
+}
+
+// Make the neighbour lists match the current grid (outside graph capture:
+// waits for the stream, then copies synchronously).
+cudaError_t batch_prepare_sync(lbm_batch* b) {
+    if (b->block > 1 || b->nbr_grid == b->grid) return cudaSuccess;
+    std::vector<int> lists;
+    b->nbr_ok = b->grid <= b->nbr_cap && batch_neighbour_lists(b, b->grid, lists);
+    b->nbr_grid = b->grid;
+    if (!b->nbr_ok) return cudaSuccess;
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = cudaMemcpy(b->d_nbr, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) b->nbr_ok = false;
+    return e;
+}
+
 cudaError_t batch_launch(lbm_batch* b, int n) {
     auto go = [&](auto tm) {
         constexpr int TM = decltype(tm)::value;
         if (b->block > 1)
             return launch_batch_tb<TM>(b->d_probs, b->d_segs, b->nsegs, n, b->block, b->rows_max, b->d_level,
                                        b->d_bar, b->d_bar + 1, b->d_status, b->grid, b->stream);
+        BatchSync sync;
+        sync.nbr = b->nbr_ok && b->nbr_grid == b->grid ? b->d_nbr : nullptr;
+        sync.done = b->d_done;
+        sync.epoch = b->d_epoch;
         return launch_batch<TM>(b->d_probs, b->d_tiles, b->ntiles, n, b->d_level, b->d_bar, b->d_bar + 1,
-                                b->d_status, b->grid, b->npt, b->stream);
+                                b->d_status, sync, b->grid, b->npt, b->stream);
     };
     switch (b->prec) {
     case LBM_FP32_T64: return go(std::integral_constant<int, T_INT64>{});
@@ -1196,6 +1262,9 @@ void lbm_batch_destroy(lbm_batch* b) {
     if (b->ev_out) cudaEventDestroy(b->ev_out);
     cudaFree(b->d_probs);
     cudaFree(b->d_tiles);
+    cudaFree(b->d_nbr);
+    cudaFree(b->d_done);
+    cudaFree(b->d_epoch);
     cudaFree(b->d_segs);
     cudaFree(b->d_level);
     cudaFree(b->d_bar);
@@ -1237,6 +1306,19 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
         for (int y0 = 0; y0 < probs[p].ny; y0 += th)
             for (int x0 = 0; x0 < probs[p].nx; x0 += tw) tiles.push_back(make_int4(p, x0, y0, 0));
     b->ntiles = (int)tiles.size();
+    b->tiles = tiles;
+    for (int p = 0, base = 0; p < nprob; ++p) {
+        const int tx = (probs[p].nx + tw - 1) / tw, ty = (probs[p].ny + th - 1) / th;
+        b->tiles_x.push_back(tx);
+        b->tiles_y.push_back(ty);
+        b->tile_base.push_back(base);
+        base += tx * ty;
+        auto periodic = [&](int side) {
+            return probs[p].bc[side].kind_lo == LBM_BC_PERIODIC || probs[p].bc[side].kind_hi == LBM_BC_PERIODIC;
+        };
+        b->periodic_x.push_back(periodic(LBM_SIDE_LEFT) || periodic(LBM_SIDE_RIGHT));
+        b->periodic_y.push_back(periodic(LBM_SIDE_BOTTOM) || periodic(LBM_SIDE_TOP));
+    }
     // temporal blocking: thin problems without periodic x sides
     b->tb_ok = true;
     for (int p = 0; p < nprob && b->tb_ok; ++p) {
@@ -1298,6 +1380,19 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
                            : prec == LBM_FP32_TDF  ? batch_max_grid<T_DF>(npt)
                            : prec == LBM_FP32_CONS ? batch_max_grid<T_CONS>(npt)
                                                    : batch_max_grid<T_INT32>(npt);
+    b->nbr_cap = b->max_grid[1] > b->max_grid[2] ? b->max_grid[1] : b->max_grid[2];
+    e = cudaMalloc((void**)&b->d_nbr, sizeof(int) * (size_t)b->nbr_cap * kBatchMaxNbr);
+    // one counter per CTA, and one more (index nbr_cap) that no CTA ever
+    // publishes to (lbm_batch_plant_stall)
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_done, sizeof(unsigned long long) * (size_t)(b->nbr_cap + 1));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_epoch, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(b->d_done, 0, sizeof(unsigned long long) * (size_t)(b->nbr_cap + 1));
+    if (e == cudaSuccess) e = cudaMemset(b->d_epoch, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) {
+        std::string m = std::string("lbm_batch_create: ") + cudaGetErrorString(e);
+        lbm_batch_destroy(b);
+        return bfail(nullptr, e == cudaErrorMemoryAllocation ? LBM_E_NOMEM : LBM_E_CUDA, m);
+    }
     b->npt = 1;
     b->grid = b->max_grid[1] < b->ntiles ? b->max_grid[1] : b->ntiles;
     if (b->tb_ok)
@@ -1318,8 +1413,15 @@ lbm_status lbm_batch_init(lbm_batch* b, const void* const* rho, const void* cons
         if (s != LBM_OK) return bfail(b, s, "problem " + std::to_string(p) + ": " + b->ctx[p]->err);
     }
     cudaSetDevice(b->device);
+    // the step counters and the grid barrier's words too: a launch that gave
+    // up may have left the counters ahead of the epoch and the barrier with
+    // arrivals that never completed
     if (cudaMemsetAsync(b->d_level, 0, sizeof(long long), b->stream) != cudaSuccess ||
-        cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), b->stream) != cudaSuccess)
+        cudaMemsetAsync(b->d_status, 0, sizeof(unsigned), b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->d_bar, 0, 2 * sizeof(unsigned), b->stream) != cudaSuccess ||
+        cudaMemsetAsync(b->d_done, 0, sizeof(unsigned long long) * (size_t)(b->nbr_cap + 1), b->stream) !=
+            cudaSuccess ||
+        cudaMemsetAsync(b->d_epoch, 0, sizeof(unsigned long long), b->stream) != cudaSuccess)
         return bfail(b, LBM_E_CUDA, "lbm_batch_init: clearing the batch state failed");
     b->step = 0;
     b->ready = true;
@@ -1332,7 +1434,8 @@ lbm_status lbm_batch_step(lbm_batch* b, int n) {
     if (!b->ready) return bfail(b, LBM_E_STATE, "lbm_batch_step before lbm_batch_init");
     if (n == 0) return LBM_OK;
     cudaSetDevice(b->device);
-    cudaError_t e = cudaSuccess;
+    cudaError_t e = batch_prepare_sync(b);
+    if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string("lbm_batch_step: ") + cudaGetErrorString(e));
     // One graph (a single cooperative kernel node) per step count, captured on
     // a private stream and replayed there, ordered after and before the
     // caller's stream by events; replays read the level from device memory,
@@ -1390,7 +1493,7 @@ lbm_status lbm_batch_sync(lbm_batch* b) {
             cudaSuccess ||
         cudaStreamSynchronize(b->stream) != cudaSuccess)
         return bfail(b, LBM_E_CUDA, "lbm_batch_sync: synchronising failed");
-    if (*b->h_status & ST_TIMEOUT) return bfail(b, LBM_E_TIMEOUT, "the batch grid barrier gave up");
+    if (*b->h_status & ST_TIMEOUT) return bfail(b, LBM_E_TIMEOUT, "a bounded wait between the batch kernel's CTAs gave up");
     if (*b->h_status & ST_NONPHYSICAL) return bfail(b, LBM_E_NONPHYSICAL, "a problem went non-physical");
     return LBM_OK;
 }
@@ -1544,6 +1647,49 @@ lbm_status lbm_batch_set_launch(lbm_batch* b, const lbm_batch_launch* l) {
     return LBM_OK;
 }
 
+lbm_status lbm_batch_set_wait_limit(double seconds) {
+    if (!(seconds > 0.0) || seconds > 60.0) return LBM_E_INVAL;
+    int dev = 0, khz = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&khz, cudaDevAttrClockRate, dev) != cudaSuccess ||
+        khz <= 0) {
+        cudaGetLastError();
+        return LBM_E_CUDA;
+    }
+    const long long cycles = (long long)(seconds * (double)khz * 1e3);
+    if (batch_set_wait_cycles(cycles < 1 ? 1 : cycles) != cudaSuccess) {
+        cudaGetLastError();
+        return LBM_E_CUDA;
+    }
+    return LBM_OK;
+}
+
+lbm_status lbm_batch_plant_stall(lbm_batch* b, int cta) {
+    if (!b) return bfail(nullptr, LBM_E_INVAL, "NULL batch");
+    cudaSetDevice(b->device);
+    cudaError_t e = cudaStreamSynchronize(b->stream);
+    if (e == cudaSuccess) e = batch_prepare_sync(b);
+    if (e != cudaSuccess) return bfail(b, LBM_E_CUDA, std::string("lbm_batch_plant_stall: ") + cudaGetErrorString(e));
+    if (cta < 0) {  // back to the lists of the current grid
+        b->nbr_grid = -1;
+        e = batch_prepare_sync(b);
+        batch_drop_graph(b);
+        return e == cudaSuccess ? LBM_OK : bfail(b, LBM_E_CUDA, "lbm_batch_plant_stall: restoring the lists failed");
+    }
+    if (b->block > 1 || !b->nbr_ok)
+        return bfail(b, LBM_E_STATE, "lbm_batch_plant_stall: the current launch shape has no neighbour lists");
+    if (cta >= b->grid)
+        return bfail(b, LBM_E_INVAL, "lbm_batch_plant_stall: cta must lie in [0, " + std::to_string(b->grid) + ")");
+    std::vector<int> lists;
+    batch_neighbour_lists(b, b->grid, lists);
+    int* row = lists.data() + (size_t)cta * kBatchMaxNbr;
+    int j = 0;
+    while (j < kBatchMaxNbr - 1 && row[j] >= 0) ++j;
+    row[j] = b->nbr_cap;  // a counter no CTA publishes to
+    e = cudaMemcpy(b->d_nbr, lists.data(), sizeof(int) * lists.size(), cudaMemcpyHostToDevice);
+    batch_drop_graph(b);
+    return e == cudaSuccess ? LBM_OK : bfail(b, LBM_E_CUDA, "lbm_batch_plant_stall: copying the lists failed");
+}
+
 lbm_status lbm_batch_get_launch(const lbm_batch* b, lbm_batch_launch* l) {
     if (!b || !l) return LBM_E_INVAL;
     l->npt = b->npt;
@@ -1614,7 +1760,8 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps, lbm_batch_launch* best, d
         b->npt = cand[k].npt;
         b->grid = cand[k].grid;
         b->block = cand[k].block;
-        e = batch_launch(b, 1);  // untimed: first launch of the variant
+        e = batch_prepare_sync(b);
+        if (e == cudaSuccess) e = batch_launch(b, 1);  // untimed: first launch of the variant
         if (e == cudaSuccess) e = restore();
         if (e == cudaSuccess) e = cudaEventRecord(t0, b->stream);
         if (e == cudaSuccess) e = batch_launch(b, steps);

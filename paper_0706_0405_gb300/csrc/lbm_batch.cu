@@ -21,6 +21,9 @@ constexpr int batch_threads() {
     return kTileW / NPT * kTileH;
 }
 constexpr long long kBarrierCycles = 4000000000LL;  // ~2 s at 2 GHz, then give up
+// SM cycles an inter-CTA wait (grid barrier, neighbour wait) lasts before it
+// gives up (batch_set_wait_cycles)
+__device__ long long g_wait_cycles = kBarrierCycles;
 constexpr uint32_t kBatchWaitLimit = 1u << 22;       // mbarrier probes before a wait gives up
 
 // Bounded grid-wide barrier for a cooperative launch.  Returns false (and
@@ -44,7 +47,7 @@ __device__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned* 
         } else {
             const long long t0 = clock64();
             while (*gen == g) {
-                if (clock64() - t0 > kBarrierCycles) {
+                if (clock64() - t0 > g_wait_cycles) {
                     atomicOr(status, ST_TIMEOUT);
                     ok = 0;
                     break;
@@ -57,6 +60,84 @@ __device__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned* 
     }
     __syncthreads();
     return ok != 0;
+}
+
+// Point-to-point step ordering between CTAs.  After its last tile of a
+// step, a CTA publishes the step count it has completed (a value that only
+// grows over the batch's life: the epoch of the launch plus the steps done);
+// before a step it waits until every CTA owning a tile next to one of its
+// own (the host's neighbour list, periodic partners included) has completed
+// the previous step.  That orders both the reads of the halo written by a
+// neighbour and the overwriting of the level a neighbour was still reading,
+// without making every CTA wait for the slowest one.  Same fences as the
+// grid barrier; the wait is bounded.
+__device__ void publish_step(unsigned long long* done, unsigned long long value) {
+    fence_proxy_async_global();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        atomicExch(done + blockIdx.x, value);
+    }
+}
+
+__device__ bool wait_neighbours(const int* __restrict__ nbr, const unsigned long long* done,
+                                unsigned long long target, unsigned* status) {
+    __shared__ int ok;
+    if (threadIdx.x == 0) {
+        ok = 1;
+        const long long t0 = clock64();
+        for (int j = 0; j < kBatchMaxNbr && ok; ++j) {
+            const int n = nbr[j];
+            if (n < 0) break;
+            while (*(volatile const unsigned long long*)(done + n) < target) {
+                if (clock64() - t0 > g_wait_cycles) {
+                    atomicOr(status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(32);
+            }
+        }
+        __threadfence();
+        fence_proxy_async_global();
+    }
+    __syncthreads();
+    return ok != 0;
+}
+
+// A problem whose whole height fits in one tile row and whose bottom and
+// top sides are periodic: its tiles hold every row of the level, so the
+// wrapped y neighbours come from the box itself and the level's y ghost rows
+// need not be stored between the steps of a launch.
+__device__ __forceinline__ bool wraps_in_tile(const Grid<float>& G, int tile_h) {
+    return G.ny <= tile_h && G.kind_lo[S_BOTTOM] == BC_PERIODIC && G.kind_hi[S_BOTTOM] == BC_PERIODIC &&
+           G.kind_lo[S_TOP] == BC_PERIODIC && G.kind_hi[S_TOP] == BC_PERIODIC;
+}
+
+// The ghost cells of level `level` that edge node (ix, iy) writes (as
+// write_ghosts), but on the left and right sides only.
+__device__ __forceinline__ void write_ghosts_x(const Grid<float>& G, float* __restrict__ f, int ix, int iy,
+                                               const float (&v)[9], long long level) {
+    const size_t pl = (size_t)G.plane;
+#pragma unroll
+    for (int side = S_LEFT; side <= S_RIGHT; ++side) {
+        const int part = side_part(G, side, iy, level);
+        const int kind = part ? G.kind_hi[side] : G.kind_lo[side];
+        const int own = side == S_LEFT ? 0 : G.nx - 1;
+        const int far = side == S_LEFT ? G.nx - 1 : 0;
+        const size_t gc = (size_t)(iy + 1) * G.row + (side == S_LEFT ? PADX - 1 : PADX + G.nx);
+        if (kind == BC_PERIODIC) {
+            if (ix == far)
+                for (int i = 0; i < 9; ++i) f[i * pl + gc] = v[i];
+        } else if (ix == own) {
+            if (kind == BC_OUTFLOW)
+                for (int i = 0; i < 9; ++i) f[i * pl + gc] = v[i];
+            else if (kind == BC_REFLECT)
+                for (int i = 0; i < 9; ++i) f[i * pl + gc] = v[mirror_x(i)];
+            else
+                for (int i = 0; i < 9; ++i) f[i * pl + gc] = G.feq[side][part][i];
+        }
+    }
 }
 
 template <typename S>
@@ -75,7 +156,8 @@ constexpr size_t kBatchSmem = 128 + sizeof(float) * 2 * kStageFloats + 2 * sizeo
 template <int TM, int NPT>
 __global__ void __launch_bounds__(batch_threads<NPT>())
     k_batch(const BatchProb* __restrict__ probs, const int4* __restrict__ tiles, int ntiles, int nsteps,
-            long long* level_ptr, unsigned* bar_count, unsigned* bar_gen, unsigned* status) {
+            long long* level_ptr, unsigned* bar_count, unsigned* bar_gen, unsigned* status,
+            const int* __restrict__ nbr, unsigned long long* done, unsigned long long* epoch_ptr) {
     __shared__ Model<float> sM;
     __shared__ Grid<float> sG;
     __shared__ int abort_flag;
@@ -92,6 +174,9 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
     }
     __syncthreads();
     const long long level0 = *(volatile long long*)level_ptr;
+    const unsigned long long epoch0 = *(volatile unsigned long long*)epoch_ptr;
+    // neighbour list of this CTA (nullptr: a grid barrier after every step)
+    const int* my_nbr = nbr ? nbr + (size_t)blockIdx.x * kBatchMaxNbr : nullptr;
     unsigned bits = 0;
     constexpr int kLanesX = kTileW / NPT;  // threads along a tile row
     const int r = tid / kLanesX, cx = tid % kLanesX;
@@ -113,11 +198,15 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
         const long long level = level0 + s;
         const int par = (int)(level & 1);
         if (*(volatile unsigned*)status & ST_TIMEOUT) return;
+        if (s > 0 && my_nbr && !wait_neighbours(my_nbr, done, epoch0 + s, status)) return;
         if (t0 < t1) {
             if (tid == 0) issue(t0, k, par);
             issued = k;
         }
         int cur = -1;
+        bool wrap = false;  // the current problem wraps in y inside its tiles
+        // y ghost rows of such problems are written on the launch's last step only
+        const bool last = s == nsteps - 1;
         for (int t = t0; t < t1; ++t, ++k) {
             // one thread waits for tile k; the barrier also says every thread
             // is done with tile k - 1 (its box and the problem constants)
@@ -142,11 +231,16 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
                            (int)(sizeof(Grid<float>) / sizeof(int)));
                 cur = T.x;
                 __syncthreads();
+                wrap = wraps_in_tile(sG, kTileH);
             }
             if constexpr (NPT == 1) {
                 const int ix = T.y + cx, iy = T.z + r;
                 if (ix < sG.nx && iy < sG.ny) {
                     const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxRow + (cx + 4);
+                    // north / south offsets in the box: across the periodic edge
+                    // of a wrapping problem, the opposite interior row
+                    const int dn = wrap && iy == sG.ny - 1 ? -(sG.ny - 1) * kBoxRow : kBoxRow;
+                    const int ds = wrap && iy == 0 ? (sG.ny - 1) * kBoxRow : -kBoxRow;
                     float f[9];
 #pragma unroll
                     for (int i = 0; i < 9; ++i) f[i] = b[i * kBoxPop];
@@ -158,21 +252,26 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         const float* bp = b + i * kBoxPop;
-                        o[i] = update(sM, i, ofe[i], f[i], bp[1], bp[-1], bp[kBoxRow], bp[-kBoxRow]);
+                        o[i] = update(sM, i, ofe[i], f[i], bp[1], bp[-1], bp[dn], bp[ds]);
                     }
                     float* fout = P.f[par ^ 1];
                     const size_t pl = (size_t)sG.plane;
                     const size_t c = cell(sG, ix, iy);
 #pragma unroll
                     for (int i = 0; i < 9; ++i) fout[i * pl + c] = o[i];
-                    if (ix == 0 || iy == 0 || ix == sG.nx - 1 || iy == sG.ny - 1)
+                    if (wrap && !last) {
+                        if (ix == 0 || ix == sG.nx - 1) write_ghosts_x(sG, fout, ix, iy, o, level + 1);
+                    } else if (ix == 0 || iy == 0 || ix == sG.nx - 1 || iy == sG.ny - 1) {
                         write_ghosts(sG, fout, ix, iy, o, level + 1);
+                    }
                 }
             } else {  // two x-adjacent nodes per thread, 8-byte shared loads and stores
                 const int ix0 = T.y + 2 * cx, iy = T.z + r;
                 if (ix0 < sG.nx && iy < sG.ny) {
                     const int nvalid = min(2, sG.nx - ix0);
                     const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxRow + (2 * cx + 4);
+                    const int dn = wrap && iy == sG.ny - 1 ? -(sG.ny - 1) * kBoxRow : kBoxRow;
+                    const int ds = wrap && iy == 0 ? (sG.ny - 1) * kBoxRow : -kBoxRow;
                     float2 C[9];
 #pragma unroll
                     for (int i = 0; i < 9; ++i) C[i] = *reinterpret_cast<const float2*>(b + i * kBoxPop);
@@ -196,8 +295,8 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
                         const float* bp = b + i * kBoxPop;
-                        const float2 Nn = *reinterpret_cast<const float2*>(bp + kBoxRow);
-                        const float2 Ss = *reinterpret_cast<const float2*>(bp - kBoxRow);
+                        const float2 Nn = *reinterpret_cast<const float2*>(bp + dn);
+                        const float2 Ss = *reinterpret_cast<const float2*>(bp + ds);
                         const float Wv = bp[-1], Ev = bp[2];
                         float2 o;
                         o.x = update(sM, i, acc[i][0], C[i].x, C[i].y, Wv, Nn.x, Ss.x);
@@ -207,7 +306,8 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
                         else
                             out[i * pl] = o.x;
                     }
-                    const bool edge_row = iy == 0 || iy == sG.ny - 1;
+                    const bool ghost_y = !(wrap && !last);
+                    const bool edge_row = ghost_y && (iy == 0 || iy == sG.ny - 1);
                     if (edge_row || ix0 == 0 || ix0 + nvalid == sG.nx) {
                         for (int j = 0; j < nvalid; ++j) {
                             const int ix = ix0 + j;
@@ -215,16 +315,28 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
                             float v[9];
 #pragma unroll
                             for (int i = 0; i < 9; ++i) v[i] = out[i * pl + j];
-                            write_ghosts(sG, fout, ix, iy, v, level + 1);
+                            if (ghost_y)
+                                write_ghosts(sG, fout, ix, iy, v, level + 1);
+                            else
+                                write_ghosts_x(sG, fout, ix, iy, v, level + 1);
                         }
                     }
                 }
             }
         }
-        if (!grid_barrier(bar_count, bar_gen, status)) return;
+        if (my_nbr)
+            publish_step(done, epoch0 + s + 1);
+        else if (!grid_barrier(bar_count, bar_gen, status))
+            return;
     }
+    // one grid barrier per launch: every CTA has read the level and epoch
+    // counters before block 0 advances them
+    if (my_nbr && !grid_barrier(bar_count, bar_gen, status)) return;
     report(status, bits);
-    if (blockIdx.x == 0 && threadIdx.x == 0) *level_ptr = level0 + nsteps;
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        *level_ptr = level0 + nsteps;
+        *epoch_ptr = epoch0 + nsteps;
+    }
 }
 // ------------------------------------------------- temporal blocking
 // For batches of thin problems (at most kTbRowsMax rows, no periodic x
@@ -390,6 +502,10 @@ __global__ void __launch_bounds__(kTbThreads, LBM_TB_MIN_BLOCKS)
 
 }  // namespace
 
+cudaError_t batch_set_wait_cycles(long long cycles) {
+    return cudaMemcpyToSymbol(g_wait_cycles, &cycles, sizeof(cycles));
+}
+
 int batch_tile_dims(int* w, int* h) {
     *w = kTileW;
     *h = kTileH;
@@ -403,12 +519,17 @@ void batch_box_dims(int* bx, int* by) {
 
 template <int TM, int NPT>
 cudaError_t launch_batch_v(const BatchProb* probs, const int4* tiles, int ntiles, int nsteps, long long* level,
-                           unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid, cudaStream_t st) {
+                           unsigned* bar_count, unsigned* bar_gen, unsigned* status, const BatchSync& sync,
+                           int grid, cudaStream_t st) {
     auto kern = k_batch<TM, NPT>;
     cudaError_t e = allow_smem<k_batch<TM, NPT>>(kBatchSmem);
     if (e != cudaSuccess) return e;
-    void* args[] = {(void*)&probs, (void*)&tiles, (void*)&ntiles, (void*)&nsteps,
-                    (void*)&level,  (void*)&bar_count, (void*)&bar_gen, (void*)&status};
+    const int* nbr = sync.nbr;
+    unsigned long long* done = sync.done;
+    unsigned long long* epoch = sync.epoch;
+    void* args[] = {(void*)&probs, (void*)&tiles, (void*)&ntiles, (void*)&nsteps, (void*)&level,
+                    (void*)&bar_count, (void*)&bar_gen, (void*)&status, (void*)&nbr, (void*)&done,
+                    (void*)&epoch};
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(batch_threads<NPT>());
@@ -424,11 +545,12 @@ cudaError_t launch_batch_v(const BatchProb* probs, const int4* tiles, int ntiles
 
 template <int TM>
 cudaError_t launch_batch(const BatchProb* probs, const int4* tiles, int ntiles, int nsteps, long long* level,
-                         unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid, int npt,
-                         cudaStream_t st) {
+                         unsigned* bar_count, unsigned* bar_gen, unsigned* status, const BatchSync& sync,
+                         int grid, int npt, cudaStream_t st) {
     if (npt == 2)
-        return launch_batch_v<TM, 2>(probs, tiles, ntiles, nsteps, level, bar_count, bar_gen, status, grid, st);
-    return launch_batch_v<TM, 1>(probs, tiles, ntiles, nsteps, level, bar_count, bar_gen, status, grid, st);
+        return launch_batch_v<TM, 2>(probs, tiles, ntiles, nsteps, level, bar_count, bar_gen, status, sync, grid,
+                                     st);
+    return launch_batch_v<TM, 1>(probs, tiles, ntiles, nsteps, level, bar_count, bar_gen, status, sync, grid, st);
 }
 
 template <int TM, int NPT>
@@ -448,7 +570,7 @@ int batch_max_grid(int npt) {
 
 #define LBM_BATCH_INST(TM)                                                                                  \
     template cudaError_t launch_batch<TM>(const BatchProb*, const int4*, int, int, long long*, unsigned*,  \
-                                          unsigned*, unsigned*, int, int, cudaStream_t);                   \
+                                          unsigned*, unsigned*, const BatchSync&, int, int, cudaStream_t); \
     template int batch_max_grid<TM>(int);
 LBM_BATCH_INST(T_INT32)
 LBM_BATCH_INST(T_INT64)

@@ -113,12 +113,25 @@ struct BatchProb {  // 128-byte aligned by its tensor maps
 };
 int batch_tile_dims(int* w, int* h);  // returns threads per CTA
 void batch_box_dims(int* bx, int* by);
+// Step ordering of the batch kernel.  nbr: kBatchMaxNbr CTA indices per CTA
+// (-1 padded), the CTAs owning a tile next to one of its own, periodic
+// partners included; nullptr orders the steps by a grid barrier instead.
+// done: one completed-step counter per CTA; epoch: steps run by the batch so
+// far (both only grow).
+constexpr int kBatchMaxNbr = 8;
+// Bound of the batch kernels' inter-CTA waits, in SM cycles (default ~2 s).
+cudaError_t batch_set_wait_cycles(long long cycles);
+struct BatchSync {
+    const int* nbr = nullptr;
+    unsigned long long* done = nullptr;
+    unsigned long long* epoch = nullptr;
+};
 // npt: nodes per thread (1: 256-thread CTAs; 2: 128-thread CTAs, two
 // x-adjacent nodes each).  grid must not exceed batch_max_grid(npt).
 template <int TM>
 cudaError_t launch_batch(const BatchProb* probs, const int4* tiles, int ntiles, int nsteps, long long* level,
-                         unsigned* bar_count, unsigned* bar_gen, unsigned* status, int grid, int npt,
-                         cudaStream_t st);
+                         unsigned* bar_count, unsigned* bar_gen, unsigned* status, const BatchSync& sync,
+                         int grid, int npt, cudaStream_t st);
 template <int TM>
 int batch_max_grid(int npt);
 // Temporal blocking for thin problems (at most rows_max rows, no periodic x

@@ -32,7 +32,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init", "lbm_step"
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_init",
            "lbm_batch_step", "lbm_batch_sync", "lbm_batch_problem", "lbm_batch_info",
            "lbm_probe_rates", "lbm_vn_scan", "lbm_batch_set_launch", "lbm_batch_get_launch",
-           "lbm_batch_autotune", "lbm_probe_tile_copy")
+           "lbm_batch_autotune", "lbm_probe_tile_copy", "lbm_batch_set_wait_limit", "lbm_batch_plant_stall")
 LBM_FLAG_NONPHYSICAL, LBM_FLAG_TIMEOUT, LBM_FLAG_T_NONPOSITIVE = 1, 2, 4
 
 
@@ -124,6 +124,8 @@ def load():
                             ctypes.c_int),
         "lbm_probe_tile_copy": ([ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)],
                                 ctypes.c_int),
+        "lbm_batch_set_wait_limit": ([ctypes.c_double], ctypes.c_int),
+        "lbm_batch_plant_stall": ([_VP, ctypes.c_int], ctypes.c_int),
         "lbm_batch_create": ([ctypes.c_int, ctypes.POINTER(lbm_problem), ctypes.c_int, _VP,
                               ctypes.POINTER(_VP)], ctypes.c_int),
         "lbm_batch_destroy": ([_VP], None),
@@ -425,6 +427,16 @@ def lbm_batch_get_launch(b):
     return l.as_tuple()
 
 
+def lbm_batch_set_wait_limit(seconds: float) -> None:
+    st = load().lbm_batch_set_wait_limit(float(seconds))
+    if st != LBM_OK:
+        raise LbmError(st, "lbm_batch_set_wait_limit failed")
+
+
+def lbm_batch_plant_stall(b, cta: int):
+    return _bcheck(b, load().lbm_batch_plant_stall(b, int(cta)))
+
+
 def lbm_batch_autotune(b, steps=10):
     """Returns ((npt, grid, block) chosen, per-step ms of each candidate)."""
     best = lbm_batch_launch()
@@ -521,6 +533,10 @@ class Batch:
 
     def get_launch(self):
         return lbm_batch_get_launch(self.handle)
+
+    def plant_stall(self, cta: int):
+        lbm_batch_plant_stall(self.handle, cta)
+        return self
 
     def autotune(self, steps: int = 10):
         return lbm_batch_autotune(self.handle, steps)

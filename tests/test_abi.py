@@ -134,3 +134,12 @@ def test_probe_tile_copy_rejects_invalid_arguments(args):
     assert lbm.load().lbm_probe_tile_copy(*args, ctypes.byref(g)) == lbm.LBM_E_INVAL
     assert lbm.load().lbm_probe_tile_copy(8, 8, 1, None) == lbm.LBM_E_INVAL
     assert g.value == -1.0
+
+
+@pytest.mark.parametrize("seconds", [0.0, -1.0, float("nan"), 61.0])
+def test_batch_wait_limit_rejects_out_of_range(seconds):
+    assert lbm.load().lbm_batch_set_wait_limit(seconds) == lbm.LBM_E_INVAL
+
+
+def test_batch_plant_stall_on_null_batch_fails_cleanly():
+    assert lbm.load().lbm_batch_plant_stall(None, 0) == lbm.LBM_E_INVAL

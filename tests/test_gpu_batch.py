@@ -114,3 +114,81 @@ def test_batch_launch_shape_errors():
         with pytest.raises(lbm.LbmError) as ei:
             b.set_launch(1, 0, 3)
         assert ei.value.status == lbm.LBM_E_INVAL
+
+
+def _mixed():
+    """Problems of 1 to 9 rows with perturbed fields: periodic in y with the
+    whole height inside one tile row (1 to 4 rows), periodic in y over two
+    tile rows (9 rows), periodic in x and y, reflecting walls."""
+    P, O, R = W.Side("periodic"), W.Side("outflow"), W.Side("reflect")
+    st = (1.0, 0.1, 0.05, 1.0)
+    return [W.uniform(100, 1, st, sides=(O, O, P, P)), W.uniform(70, 2, st, sides=(P, P, P, P)),
+            W.uniform(130, 3, st, sides=(O, O, P, P)), W.uniform(64, 4, st, sides=(P, P, P, P)),
+            W.uniform(90, 9, st, sides=(O, O, P, P)), W.uniform(50, 5, st, sides=(O, O, R, R)),
+            W.uniform(200, 4, st, sides=(O, O, P, P))]
+
+
+@pytest.mark.parametrize("shape", [(1, 0, 0), (2, 0, 0), (1, 3, 0), (2, 2, 0)])
+def test_mixed_heights_and_sides_equal_problems_stepped_alone(shape):
+    """Heights 1 to 9 and every y rule: problems whose tile holds every row
+    take their periodic y neighbours from the tile and write their y ghost
+    rows on a launch's last step only; over several calls of several steps
+    the levels equal those of each problem stepped alone, bit for bit."""
+    probs = _mixed()
+    fields = [W.initial_fields(p, seed=k, sigma=0.01) for k, p in enumerate(probs)]
+    with lbm.Batch(probs, "fp32_cons") as b:
+        b.init(fields).set_launch(*shape).step(25).step(1).step(34)
+        b.sync()
+        got = [b.get_f(k).cpu().numpy() for k in range(len(probs))]
+    for p, fl, g in zip(probs, fields, got):
+        with lbm.Lattice(p, "fp32_cons") as lat:
+            lat.init(*fl).step(60)
+            want = lat.get_f().cpu().numpy()
+        assert np.array_equal(g, want), p.name
+
+
+def test_switching_to_temporal_blocking_mid_run_keeps_the_bits():
+    """The tile kernel leaves the level with valid ghost rows at the end of
+    every launch, so the temporal-blocking kernel (which reads them) can take
+    over between calls."""
+    probs = _subset()
+    fields = [W.initial_fields(p) for p in probs]
+    with lbm.Batch(probs, "fp32_cons") as b:
+        b.init(fields).step(50).set_launch(1, 0, 3).step(50).set_launch(2, 0, 0).step(20)
+        b.sync()
+        got = [b.get_f(k).cpu().numpy() for k in range(len(probs))]
+    for p, fl, g in zip(probs, fields, got):
+        with lbm.Lattice(p, "fp32_cons") as lat:
+            lat.init(*fl).step(120)
+            want = lat.get_f().cpu().numpy()
+        assert np.array_equal(g, want), p.name
+
+
+def test_a_neighbour_that_never_finishes_times_out_and_the_batch_recovers():
+    """Failure injected on the host: one CTA is told to wait for a counter no
+    CTA advances.  Its bounded wait runs out (0.2 s here), the launch stops,
+    LBM_E_TIMEOUT reaches the caller, and after lbm_batch_init the same batch
+    steps correctly again (bit for bit against each problem alone)."""
+    probs = _subset()
+    fields = [W.initial_fields(p) for p in probs]
+    lbm.lbm_batch_set_wait_limit(0.2)
+    try:
+        with lbm.Batch(probs, "fp32_cons") as b:
+            b.set_launch(1, 0, 0).init(fields).step(3)
+            b.sync()
+            b.plant_stall(1)
+            with pytest.raises(lbm.LbmError) as ei:
+                b.step(6)
+                b.sync()
+            assert ei.value.status == lbm.LBM_E_TIMEOUT
+            b.plant_stall(-1)
+            b.init(fields).step(10)
+            b.sync()
+            got = [b.get_f(k).cpu().numpy() for k in range(len(probs))]
+    finally:
+        lbm.lbm_batch_set_wait_limit(2.0)
+    for p, fl, g in zip(probs, fields, got):
+        with lbm.Lattice(p, "fp32_cons") as lat:
+            lat.init(*fl).step(10)
+            want = lat.get_f().cpu().numpy()
+        assert np.array_equal(g, want), p.name
