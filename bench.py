@@ -482,7 +482,9 @@ def profile_case(args):
         probs = W.batch_riemann()
         side = torch.cuda.Stream()
         with lbm.Batch(probs, args.precision, stream=side.cuda_stream) as b:
-            b.init([W.initial_fields(q) for q in probs]).step(20)
+            # two nodes per thread on a full wave: the shape the autotuner
+            # keeps on this workload
+            b.set_launch(2, 0, 0).init([W.initial_fields(q) for q in probs]).step(20)
             b.sync()
     else:
         q = W.mach3_2048x256(steps=20)

@@ -184,7 +184,13 @@ __global__ void k_adjoint_wrap(float* __restrict__ a, const Grid<float> G) {
 // the level filled (write_periodic_ghosts).  One thread waits (bounded; on
 // give-up the CTA raises ST_TIMEOUT, drains its copies and returns) while the
 // others sleep in the barrier, which also frees the previous stage.
-constexpr int kAdjTX = 64, kAdjTY = 4, kAdjThreads = kAdjTX * kAdjTY;
+#ifndef LBM_ADJ_TY
+#define LBM_ADJ_TY 4
+#endif
+#ifndef LBM_ADJ_MIN_BLOCKS
+#define LBM_ADJ_MIN_BLOCKS 3
+#endif
+constexpr int kAdjTX = 64, kAdjTY = LBM_ADJ_TY, kAdjThreads = kAdjTX * kAdjTY;
 constexpr int kAdjBoxX = kAdjTX + 8, kAdjBoxY = kAdjTY + 2;
 constexpr int kAdjAFloats = kAdjBoxX * kAdjBoxY * 9;
 constexpr int kAdjAPad = (kAdjAFloats + 31) / 32 * 32;  // the f box starts on a 128-byte boundary
@@ -194,7 +200,7 @@ constexpr size_t kAdjSmem = 128 + sizeof(float) * 2 * kAdjStageFloats + 2 * size
 constexpr uint32_t kAdjWaitLimit = 1u << 22;
 
 template <int TM>
-__global__ void __launch_bounds__(kAdjThreads, 3)
+__global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS)
     k_adjoint_tile(const __grid_constant__ CUtensorMap tmapA, const __grid_constant__ CUtensorMap tmapF,
                    float* __restrict__ abar, const Model<float> M,
                    const Grid<float> G, long long level, double* __restrict__ taup, int tiles_x, int ntiles,
