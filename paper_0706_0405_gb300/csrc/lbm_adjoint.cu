@@ -31,13 +31,14 @@ __device__ __forceinline__ void adjoint_core(const Model<S>& M, const S (&fv)[9]
                                              const S (&aU)[9], S (&o)[9], S& tn) {
     S rho, ux, uy, T;
     moments<S, TM>(fv, M, rho, ux, uy, T);
-    S fe[9];
-    equilibrium(M, rho, ux, uy, T, fe);
-    tn = S(0);
-#pragma unroll
-    for (int i = 0; i < 9; ++i) tn = fma_(av[i], sub_(fe[i], fv[i]), tn);
     S h[4], g[9];
     feq_vjp(M, rho, ux, uy, T, av, h);
+    // tau term: f^eq is linear in rho, so sum_i a_i f^eq_i = rho dF/drho . a
+    // = rho h[0]; no equilibrium needs evaluating
+    S af = mul_(av[0], fv[0]);
+#pragma unroll
+    for (int i = 1; i < 9; ++i) af = fma_(av[i], fv[i], af);
+    tn = fma_(rho, h[0], neg_(af));
     moments_vjp(M, rho, ux, uy, T, h, g);
 #pragma unroll
     for (int j = 0; j < 9; ++j) {

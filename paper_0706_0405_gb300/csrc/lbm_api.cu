@@ -1175,11 +1175,10 @@ lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& msg) {
     return s;
 }
 
-// For each CTA of a grid (CTA c walks tiles [c per, (c + 1) per)), the
-// other CTAs owning a tile next to one of its tiles in x or y, across
-// periodic sides too.  False if some CTA has more than kBatchMaxNbr.
+// For each CTA of a grid, the other CTAs owning a tile next to one of its
+// tiles in x or y, across periodic sides too.  False if some CTA has more
+// than kBatchMaxNbr.
 bool batch_neighbour_lists(const lbm_batch* b, int grid, std::vector<int>& out) {
-    const int per = (b->ntiles + grid - 1) / grid;
     out.assign((size_t)grid * kBatchMaxNbr, -1);
     std::vector<int> cnt(grid, 0);
     auto add = [&](int c, int n) {
@@ -1195,7 +1194,7 @@ bool batch_neighbour_lists(const lbm_batch* b, int grid, std::vector<int>& out) 
     for (int t = 0; t < b->ntiles; ++t) {
         const int4 T = b->tiles[t];
         const int p = T.x, tx = b->tiles_x[p], ty = b->tiles_y[p];
-        const int ix = T.y / tw, iy = T.z / th, c = t / per;
+        const int ix = T.y / tw, iy = T.z / th, c = batch_tile_owner(t, b->ntiles, grid);
         const int nb[4][2] = {{ix - 1, iy}, {ix + 1, iy}, {ix, iy - 1}, {ix, iy + 1}};
         for (const auto& q : nb) {
             int jx = q[0], jy = q[1];
@@ -1207,7 +1206,7 @@ bool batch_neighbour_lists(const lbm_batch* b, int grid, std::vector<int>& out) 
                 if (!b->periodic_y[p]) continue;
                 jy = (jy + ty) % ty;
             }
-            if (!add(c, (b->tile_base[p] + jy * tx + jx) / per)) return false;
+            if (!add(c, batch_tile_owner(b->tile_base[p] + jy * tx + jx, b->ntiles, grid))) return false;
         }
     }
     return true;

@@ -145,6 +145,10 @@ __device__ __forceinline__ void copy_words(S* dst, const S* src, int n) {
     for (int k = threadIdx.x; k < n; k += blockDim.x) dst[k] = src[k];
 }
 
+#ifndef LBM_BATCH_STRIDED
+#define LBM_BATCH_STRIDED 0
+#endif
+constexpr bool kBatchStrided = LBM_BATCH_STRIDED != 0;
 constexpr int kBoxW = kTileW + 8;  // 4 extra columns each side keep 16-byte alignment
 constexpr int kBoxH = kTileH + 2;
 // The box in shared memory is [row][population][column], like the level.
@@ -180,10 +184,18 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
     unsigned bits = 0;
     constexpr int kLanesX = kTileW / NPT;  // threads along a tile row
     const int r = tid / kLanesX, cx = tid % kLanesX;
-    // a contiguous run of tiles per CTA: consecutive tiles mostly share a
-    // problem, so its constants are copied to shared memory rarely
-    const int per = (ntiles + gridDim.x - 1) / gridDim.x;
-    const int t0 = blockIdx.x * per, t1 = min(ntiles, t0 + per);
+    // this CTA's tiles: t0, t0 + stride, ... below t1 (batch_tile_owner)
+    int t0, t1, stride;
+    if (kBatchStrided) {  // every gridDim.x-th tile: concurrent CTAs work on neighbouring tiles
+        t0 = blockIdx.x;
+        t1 = ntiles;
+        stride = gridDim.x;
+    } else {  // a contiguous run: consecutive tiles mostly share a problem
+        const int per = (ntiles + gridDim.x - 1) / gridDim.x;
+        t0 = blockIdx.x * per;
+        t1 = min(ntiles, t0 + per);
+        stride = 1;
+    }
     // running index k of this CTA's tiles over all steps: stage k & 1,
     // phase parity (k >> 1) & 1
     auto issue = [&](int t, int k, int par) {
@@ -207,7 +219,7 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
         bool wrap = false;  // the current problem wraps in y inside its tiles
         // y ghost rows of such problems are written on the launch's last step only
         const bool last = s == nsteps - 1;
-        for (int t = t0; t < t1; ++t, ++k) {
+        for (int t = t0; t < t1; t += stride, ++k) {
             // one thread waits for tile k; the barrier also says every thread
             // is done with tile k - 1 (its box and the problem constants)
             if (tid == 0 && !wait(k)) abort_flag = 1;
@@ -218,8 +230,8 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
                 return;
             }
             waited = k;
-            if (t + 1 < t1) {
-                if (tid == 0) issue(t + 1, k + 1, par);
+            if (t + stride < t1) {
+                if (tid == 0) issue(t + stride, k + 1, par);
                 issued = k + 1;
             }
             const int4 T = tiles[t];
@@ -501,6 +513,10 @@ __global__ void __launch_bounds__(kTbThreads, LBM_TB_MIN_BLOCKS)
 }
 
 }  // namespace
+
+int batch_tile_owner(int t, int ntiles, int grid) {
+    return kBatchStrided ? t % grid : t / ((ntiles + grid - 1) / grid);
+}
 
 cudaError_t batch_set_wait_cycles(long long cycles) {
     return cudaMemcpyToSymbol(g_wait_cycles, &cycles, sizeof(cycles));

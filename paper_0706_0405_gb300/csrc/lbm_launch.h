@@ -119,6 +119,8 @@ void batch_box_dims(int* bx, int* by);
 // done: one completed-step counter per CTA; epoch: steps run by the batch so
 // far (both only grow).
 constexpr int kBatchMaxNbr = 8;
+// The CTA of a grid of `grid` that walks tile t of the batch kernel.
+int batch_tile_owner(int t, int ntiles, int grid);
 // Bound of the batch kernels' inter-CTA waits, in SM cycles (default ~2 s).
 cudaError_t batch_set_wait_cycles(long long cycles);
 struct BatchSync {
