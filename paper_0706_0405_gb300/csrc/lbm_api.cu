@@ -1342,8 +1342,12 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
         hp[p].f[1] = static_cast<float*>(b->ctx[p]->f[1]);
         hp[p].M = b->ctx[p]->mf;
         hp[p].G = b->ctx[p]->gf;
+        // a problem that wraps in y inside its tile needs only its interior rows
+        hp[p].wrap = batch_wraps_in_tile(hp[p].G) ? 1 : 0;
+        const int rows = hp[p].wrap ? th : bby;
+        hp[p].box_bytes = (unsigned)(sizeof(float) * 9 * bbx * rows);
         for (int k = 0; k < 2; ++k)
-            if (!make_tmap_box(&hp[p].tm[k], b->ctx[p]->f[k], *b->ctx[p], bbx, bby)) {
+            if (!make_tmap_box(&hp[p].tm[k], b->ctx[p]->f[k], *b->ctx[p], bbx, rows)) {
                 lbm_batch_destroy(b);
                 return bfail(nullptr, LBM_E_CUDA, "lbm_batch_create: tensor maps unavailable on this driver");
             }

@@ -109,7 +109,7 @@ __device__ bool wait_neighbours(const int* __restrict__ nbr, const unsigned long
 // top sides are periodic: its tiles hold every row of the level, so the
 // wrapped y neighbours come from the box itself and the level's y ghost rows
 // need not be stored between the steps of a launch.
-__device__ __forceinline__ bool wraps_in_tile(const Grid<float>& G, int tile_h) {
+__host__ __device__ __forceinline__ bool wraps_in_tile(const Grid<float>& G, int tile_h) {
     return G.ny <= tile_h && G.kind_lo[S_BOTTOM] == BC_PERIODIC && G.kind_hi[S_BOTTOM] == BC_PERIODIC &&
            G.kind_lo[S_TOP] == BC_PERIODIC && G.kind_hi[S_TOP] == BC_PERIODIC;
 }
@@ -200,9 +200,11 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
     // phase parity (k >> 1) & 1
     auto issue = [&](int t, int k, int par) {
         const int4 T = tiles[t];
-        mbar_arrive_expect_tx(&bar[k & 1], (uint32_t)(sizeof(float) * kBoxFloats));
-        // array column T.y (interior column T.y - 4), array row T.z (interior row T.z - 1)
-        tma_load_3d(box0 + (k & 1) * kStageFloats, &probs[T.x].tm[par], T.y, 0, T.z, &bar[k & 1]);
+        const BatchProb& Q = probs[T.x];
+        mbar_arrive_expect_tx(&bar[k & 1], Q.box_bytes);
+        // array column T.y (interior column T.y - 4), array row T.z (interior row T.z - 1);
+        // a wrapping problem's box starts one row lower, at its first interior row
+        tma_load_3d(box0 + (k & 1) * kStageFloats, &Q.tm[par], T.y, 0, T.z + Q.wrap, &bar[k & 1]);
     };
     auto wait = [&](int k) { return mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), kBatchWaitLimit); };
     int k = 0, issued = -1, waited = -1;
@@ -248,7 +250,8 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
             if constexpr (NPT == 1) {
                 const int ix = T.y + cx, iy = T.z + r;
                 if (ix < sG.nx && iy < sG.ny) {
-                    const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxRow + (cx + 4);
+                    // box row of interior row iy: iy + 1, or iy for a wrapping problem
+                    const float* b = box0 + (k & 1) * kStageFloats + (r + !wrap) * kBoxRow + (cx + 4);
                     // north / south offsets in the box: across the periodic edge
                     // of a wrapping problem, the opposite interior row
                     const int dn = wrap && iy == sG.ny - 1 ? -(sG.ny - 1) * kBoxRow : kBoxRow;
@@ -281,7 +284,7 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
                 const int ix0 = T.y + 2 * cx, iy = T.z + r;
                 if (ix0 < sG.nx && iy < sG.ny) {
                     const int nvalid = min(2, sG.nx - ix0);
-                    const float* b = box0 + (k & 1) * kStageFloats + (r + 1) * kBoxRow + (2 * cx + 4);
+                    const float* b = box0 + (k & 1) * kStageFloats + (r + !wrap) * kBoxRow + (2 * cx + 4);
                     const int dn = wrap && iy == sG.ny - 1 ? -(sG.ny - 1) * kBoxRow : kBoxRow;
                     const int ds = wrap && iy == 0 ? (sG.ny - 1) * kBoxRow : -kBoxRow;
                     float2 C[9];
@@ -513,6 +516,8 @@ __global__ void __launch_bounds__(kTbThreads, LBM_TB_MIN_BLOCKS)
 }
 
 }  // namespace
+
+bool batch_wraps_in_tile(const Grid<float>& G) { return wraps_in_tile(G, kTileH); }
 
 int batch_tile_owner(int t, int ntiles, int grid) {
     return kBatchStrided ? t % grid : t / ((ntiles + grid - 1) / grid);

@@ -106,11 +106,17 @@ cudaError_t launch_feq_vjp(const S* r, const S* ux, const S* uy, const S* T, con
 
 // Batch (lbm_batch.cu): FP32 problems advanced by one cooperative launch.
 struct BatchProb {  // 128-byte aligned by its tensor maps
-    CUtensorMap tm[2];  // tensor maps of the two levels (box: batch_box_dims x 9)
+    CUtensorMap tm[2];  // tensor maps of the two levels (box: batch_box_dims, or for
+                        // `wrap` problems its interior rows only, x 9)
     float* f[2];        // the two levels; level k lives in f[k & 1]
     Model<float> M;
     Grid<float> G;
+    int wrap;           // batch_wraps_in_tile(G): boxes start at the first interior row
+    unsigned box_bytes; // bytes of one box
 };
+// The problem's height fits in one tile row and its y sides are periodic:
+// the batch kernel takes the wrapped y neighbours from inside the tile.
+bool batch_wraps_in_tile(const Grid<float>& G);
 int batch_tile_dims(int* w, int* h);  // returns threads per CTA
 void batch_box_dims(int* bx, int* by);
 // Step ordering of the batch kernel.  nbr: kBatchMaxNbr CTA indices per CTA
