@@ -25,13 +25,14 @@ __device__ __forceinline__ int kind_at(const Grid<S>& G, int side, int along_ind
 // non-periodic side), the adjoint of level n at the node (o) before the ghost
 // links, and the node's tau term tn = sum_i a_i (f^eq_i - f_i).  Both adjoint
 // kernels use it, so they round alike.
+// The collision part: g = (df^eq/df)^T a at the node (through the moments)
+// and the tau term tn.
 template <typename S, int TM>
-__device__ __forceinline__ void adjoint_core(const Model<S>& M, const S (&fv)[9], const S (&av)[9],
-                                             const S (&aL)[9], const S (&aR)[9], const S (&aD)[9],
-                                             const S (&aU)[9], S (&o)[9], S& tn) {
+__device__ __forceinline__ void adjoint_collision(const Model<S>& M, const S (&fv)[9], const S (&av)[9],
+                                                  S (&g)[9], S& tn) {
     S rho, ux, uy, T;
     moments<S, TM>(fv, M, rho, ux, uy, T);
-    S h[4], g[9];
+    S h[4];
     feq_vjp(M, rho, ux, uy, T, av, h);
     // tau term: f^eq is linear in rho, so sum_i a_i f^eq_i = rho dF/drho . a
     // = rho h[0]; no equilibrium needs evaluating
@@ -40,14 +41,28 @@ __device__ __forceinline__ void adjoint_core(const Model<S>& M, const S (&fv)[9]
     for (int i = 1; i < 9; ++i) af = fma_(av[i], fv[i], af);
     tn = fma_(rho, h[0], neg_(af));
     moments_vjp(M, rho, ux, uy, T, h, g);
+}
+
+// Adjoint of population j of one node from the transposed star: its own
+// weight with the collision term, then the nodes left of, right of, below
+// and above it, which read it as their E, W, N and S neighbour.
+template <typename S>
+__device__ __forceinline__ S adjoint_star(const Model<S>& M, int j, S g, S a, S aL, S aR, S aD, S aU) {
+    S r = fma_(M.w[j][0], a, mul_(M.omega, g));
+    r = fma_(M.w[j][1], aL, r);
+    r = fma_(M.w[j][2], aR, r);
+    r = fma_(M.w[j][3], aD, r);
+    return fma_(M.w[j][4], aU, r);
+}
+
+template <typename S, int TM>
+__device__ __forceinline__ void adjoint_core(const Model<S>& M, const S (&fv)[9], const S (&av)[9],
+                                             const S (&aL)[9], const S (&aR)[9], const S (&aD)[9],
+                                             const S (&aU)[9], S (&o)[9], S& tn) {
+    S g[9];
+    adjoint_collision<S, TM>(M, fv, av, g, tn);
 #pragma unroll
-    for (int j = 0; j < 9; ++j) {
-        S r = fma_(M.w[j][0], av[j], mul_(M.omega, g[j]));
-        r = fma_(M.w[j][1], aL[j], r);  // the node left of me reads me as E
-        r = fma_(M.w[j][2], aR[j], r);  // the node right of me reads me as W
-        r = fma_(M.w[j][3], aD[j], r);  // the node below reads me as N
-        o[j] = fma_(M.w[j][4], aU[j], r);  // the node above reads me as S
-    }
+    for (int j = 0; j < 9; ++j) o[j] = adjoint_star(M, j, g[j], av[j], aL[j], aR[j], aD[j], aU[j]);
 }
 
 // Ghost links of an edge node: its own ghost cell on a non-periodic side is
@@ -84,14 +99,18 @@ __device__ __forceinline__ void write_periodic_ghosts(const Grid<S>& G, S* __res
     const size_t pl = (size_t)G.plane;
     if (G.kind_lo[S_LEFT] == BC_PERIODIC) {
         if (ix == G.nx - 1)
+#pragma unroll
             for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(iy + 1) * G.row + (PADX - 1)] = v[i];
         if (ix == 0)
+#pragma unroll
             for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(iy + 1) * G.row + (PADX + G.nx)] = v[i];
     }
     if (G.kind_lo[S_BOTTOM] == BC_PERIODIC) {
         if (iy == G.ny - 1)
+#pragma unroll
             for (int i = 0; i < 9; ++i) a[i * pl + (size_t)ix + PADX] = v[i];
         if (iy == 0)
+#pragma unroll
             for (int i = 0; i < 9; ++i) a[i * pl + (size_t)(G.ny + 1) * G.row + ix + PADX] = v[i];
     }
 }
@@ -188,10 +207,14 @@ __global__ void k_adjoint_wrap(float* __restrict__ a, const Grid<float> G) {
 #ifndef LBM_ADJ_TY
 #define LBM_ADJ_TY 4
 #endif
-#ifndef LBM_ADJ_MIN_BLOCKS
-#define LBM_ADJ_MIN_BLOCKS 3
+#ifndef LBM_ADJ_NPT
+#define LBM_ADJ_NPT 1
 #endif
-constexpr int kAdjTX = 64, kAdjTY = LBM_ADJ_TY, kAdjThreads = kAdjTX * kAdjTY;
+#ifndef LBM_ADJ_MIN_BLOCKS
+#define LBM_ADJ_MIN_BLOCKS (LBM_ADJ_NPT == 2 ? 4 : 3)
+#endif
+constexpr int kAdjTX = 64, kAdjTY = LBM_ADJ_TY, kAdjNpt = LBM_ADJ_NPT;
+constexpr int kAdjThreads = kAdjTX / kAdjNpt * kAdjTY;  // kAdjNpt x-adjacent nodes per thread
 constexpr int kAdjBoxX = kAdjTX + 8, kAdjBoxY = kAdjTY + 2;
 constexpr int kAdjAFloats = kAdjBoxX * kAdjBoxY * 9;
 constexpr int kAdjAPad = (kAdjAFloats + 31) / 32 * 32;  // the f box starts on a 128-byte boundary
@@ -212,7 +235,8 @@ __global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS)
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(float) * 2 * kAdjStageFloats);
     __shared__ int abort_flag;
     __shared__ double wsum_sh[kAdjThreads / 32];
-    const int tid = threadIdx.x, tx = tid % kAdjTX, ty = tid / kAdjTX;
+    constexpr int kLanesX = kAdjTX / kAdjNpt;
+    const int tid = threadIdx.x, tx = tid % kLanesX, ty = tid / kLanesX;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
         mbar_init(&bar[1], 1);
@@ -255,33 +279,98 @@ __global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS)
             if (tid == 0) issue(t + gridDim.x, (k + 1) & 1);
             issued = k + 1;
         }
-        const int ix = (t % tiles_x) * kAdjTX + tx, iy = (t / tiles_x) * kAdjTY + ty;
         float tn = 0.0f;
-        if (ix < G.nx && iy < G.ny) {
-            const float* sA = stage0 + (k & 1) * kAdjStageFloats + (ty + 1) * RA + (tx + 4);
-            const float* sF = stage0 + (k & 1) * kAdjStageFloats + kAdjAPad + ty * RF + tx;
-            // the box holds the star of every node: interior neighbours, the
-            // wrapped values in the ghost cells of periodic sides, zeros in
-            // the ghost cells of the others
-            float fv[9], av[9], aL[9], aR[9], aD[9], aU[9], o[9];
+        if constexpr (kAdjNpt == 1) {
+            const int ix = (t % tiles_x) * kAdjTX + tx, iy = (t / tiles_x) * kAdjTY + ty;
+            if (ix < G.nx && iy < G.ny) {
+                const float* sA = stage0 + (k & 1) * kAdjStageFloats + (ty + 1) * RA + (tx + 4);
+                const float* sF = stage0 + (k & 1) * kAdjStageFloats + kAdjAPad + ty * RF + tx;
+                // the box holds the star of every node: interior neighbours, the
+                // wrapped values in the ghost cells of periodic sides, zeros in
+                // the ghost cells of the others
+                float fv[9], av[9], aL[9], aR[9], aD[9], aU[9], o[9];
 #pragma unroll
-            for (int i = 0; i < 9; ++i) {
-                const float* pA = sA + i * PA;
-                fv[i] = sF[i * PF];
-                av[i] = pA[0];
-                aL[i] = pA[-1];
-                aR[i] = pA[1];
-                aD[i] = pA[-RA];
-                aU[i] = pA[RA];
-            }
-            adjoint_core<float, TM>(M, fv, av, aL, aR, aD, aU, o, tn);
-            const size_t c = cell(G, ix, iy);
-            if (ix == 0 || iy == 0 || ix == G.nx - 1 || iy == G.ny - 1) {
-                adjoint_ghost_links(M, G, level, ix, iy, av, o);
-                write_periodic_ghosts(G, abar, ix, iy, o);
-            }
+                for (int i = 0; i < 9; ++i) {
+                    const float* pA = sA + i * PA;
+                    fv[i] = sF[i * PF];
+                    av[i] = pA[0];
+                    aL[i] = pA[-1];
+                    aR[i] = pA[1];
+                    aD[i] = pA[-RA];
+                    aU[i] = pA[RA];
+                }
+                adjoint_core<float, TM>(M, fv, av, aL, aR, aD, aU, o, tn);
+                const size_t c = cell(G, ix, iy);
+                if (ix == 0 || iy == 0 || ix == G.nx - 1 || iy == G.ny - 1) {
+                    adjoint_ghost_links(M, G, level, ix, iy, av, o);
+                    write_periodic_ghosts(G, abar, ix, iy, o);
+                }
 #pragma unroll
-            for (int j = 0; j < 9; ++j) abar[j * pl + c] = o[j];
+                for (int j = 0; j < 9; ++j) abar[j * pl + c] = o[j];
+            }
+        } else {  // two x-adjacent nodes per thread: 8-byte shared loads and stores
+            const int ix0 = (t % tiles_x) * kAdjTX + 2 * tx, iy = (t / tiles_x) * kAdjTY + ty;
+            if (ix0 < G.nx && iy < G.ny) {
+                const int nvalid = min(2, G.nx - ix0);
+                const float* sA = stage0 + (k & 1) * kAdjStageFloats + (ty + 1) * RA + (2 * tx + 4);
+                const float* sF = stage0 + (k & 1) * kAdjStageFloats + kAdjAPad + ty * RF + 2 * tx;
+                float2 A2[9];
+                float g[2][9];
+                float tt[2];
+#pragma unroll
+                for (int i = 0; i < 9; ++i) A2[i] = *reinterpret_cast<const float2*>(sA + i * PA);
+#pragma unroll
+                for (int n = 0; n < 2; ++n) {
+                    float fv[9], av[9];
+#pragma unroll
+                    for (int i = 0; i < 9; ++i) {
+                        fv[i] = sF[i * PF + n];
+                        av[i] = n ? A2[i].y : A2[i].x;
+                    }
+                    adjoint_collision<float, TM>(M, fv, av, g[n], tt[n]);
+                }
+                // a node past the right edge (odd nx) has f = 0 in the box:
+                // its terms are not used
+                tn = nvalid == 2 ? add_(tt[0], tt[1]) : tt[0];
+                float o[2][9];
+#pragma unroll
+                for (int j = 0; j < 9; ++j) {
+                    const float* pA = sA + j * PA;
+                    const float2 Nn = *reinterpret_cast<const float2*>(pA + RA);
+                    const float2 Ss = *reinterpret_cast<const float2*>(pA - RA);
+                    const float Wv = pA[-1], Ev = pA[2];
+                    o[0][j] = adjoint_star(M, j, g[0][j], A2[j].x, Wv, A2[j].y, Ss.x, Nn.x);
+                    o[1][j] = adjoint_star(M, j, g[1][j], A2[j].y, A2[j].x, Ev, Ss.y, Nn.y);
+                }
+                float* out = abar + cell(G, ix0, iy);  // 8-byte aligned: ix0 + PADX is even
+#pragma unroll
+                for (int j = 0; j < 9; ++j) {
+                    if (nvalid == 2)
+                        *reinterpret_cast<float2*>(out + j * pl) = make_float2(o[0][j], o[1][j]);
+                    else
+                        out[j * pl] = o[0][j];
+                }
+                // edge nodes: the ghost links, on the values just stored (read
+                // back) and the node's adjoint from the box
+                const bool edge_row = iy == 0 || iy == G.ny - 1;
+                if (edge_row || ix0 == 0 || ix0 + nvalid == G.nx) {
+#pragma unroll 1
+                    for (int n = 0; n < nvalid; ++n) {
+                        const int ix = ix0 + n;
+                        if (!(edge_row || ix == 0 || ix == G.nx - 1)) continue;
+                        float av[9], on[9];
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) {
+                            av[i] = sA[i * PA + n];
+                            on[i] = out[i * pl + n];
+                        }
+                        adjoint_ghost_links(M, G, level, ix, iy, av, on);
+                        write_periodic_ghosts(G, abar, ix, iy, on);
+#pragma unroll
+                        for (int i = 0; i < 9; ++i) out[i * pl + n] = on[i];
+                    }
+                }
+            }
         }
 #pragma unroll
         for (int s = 16; s > 0; s >>= 1) tn += __shfl_down_sync(0xffffffffu, tn, s);
