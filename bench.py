@@ -418,9 +418,41 @@ def cpu_baseline(p, seconds, threads=None):
     t0 = time.perf_counter()
     oracle.run(p, f, n, 1)
     el = time.perf_counter() - t0
-    return {"value": round(p.nodes * n / el / 1e9, 6), "unit": "GLUPS", "cores": threads,
-            "kind": "oracle",
-            "sample": f"FP64 oracle on {p.name}, {n} whole steps (steps 1..{n}) in {el:.1f} s"}
+    out = {"value": round(p.nodes * n / el / 1e9, 6), "unit": "GLUPS", "cores": threads,
+           "kind": "oracle",
+           "sample": f"FP64 oracle on {p.name}, {n} whole steps (steps 1..{n}) in {el:.1f} s",
+           "cpu_model": cpu_model()}
+    if threads > 1:  # the same oracle on one core, a few whole steps
+        oracle.set_threads(1)
+        f = oracle.init(p, *W.initial_fields(p))
+        m = max(1, int(min(seconds, 4.0) / max(one * threads, 1e-6)))
+        t0 = time.perf_counter()
+        oracle.run(p, f, m, 0)
+        el1 = time.perf_counter() - t0
+        out["serial"] = {"value": round(p.nodes * m / el1 / 1e9, 6), "unit": "GLUPS", "cores": 1,
+                         "sample": f"{m} whole steps (steps 0..{m - 1}) in {el1:.1f} s"}
+        oracle.set_threads(threads)
+    return out
+
+
+def cpu_model() -> str:
+    """The host CPU's model name (lscpu, else /proc/cpuinfo, else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
 
 
 def reference_arm(args, world, budget_s=120.0):
