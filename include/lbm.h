@@ -409,6 +409,13 @@ lbm_status lbm_batch_autotune(lbm_batch* batch, int steps, lbm_batch_launch* bes
 lbm_status lbm_batch_set_wait_limit(double seconds);
 lbm_status lbm_batch_plant_stall(lbm_batch* batch, int cta);
 
+/* Failure injection for tests, on the host side: after `after` more device
+ * allocations by the library succeed, the next one fails as if the device
+ * were out of memory (and the countdown stops); after < 0 switches it off.
+ * The failing call returns LBM_E_NOMEM and frees what it had allocated.
+ * Process-wide; always LBM_OK. */
+lbm_status lbm_inject_alloc_failure(long long after);
+
 /* -------------------------------------------------- von Neumann scanner
  * Linear stability of the scheme about a uniform state (Sec. 3): a Fourier
  * mode exp(i k.x) of a perturbation of f is multiplied each step by the 9 x 9

@@ -1,6 +1,7 @@
 // lbm_api.cu -- the C ABI of liblbm (declared in include/lbm.h): context
 // lifetime, parameter checks, derived constants, buffer management and the
 // calls that queue the kernels on the caller's stream.
+#include <atomic>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -12,6 +13,32 @@
 
 #include "../../include/lbm.h"
 #include "lbm_launch.h"
+
+// NVTX ranges around the entry points (header-only NVTX 3: a no-op unless a
+// profiler that collects them is attached).
+#include <nvtx3/nvToolsExt.h>
+namespace {
+struct NvtxRange {
+    explicit NvtxRange(const char* name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange&) = delete;
+    NvtxRange& operator=(const NvtxRange&) = delete;
+};
+
+// Every device allocation of the library goes through dev_malloc, so that a
+// test can make the n-th one fail (lbm_inject_alloc_failure) and check that
+// the failure surfaces as LBM_E_NOMEM and leaks nothing.
+std::atomic<long long> g_alloc_countdown{-1};
+
+template <typename T>
+cudaError_t dev_malloc(T** p, size_t bytes) {
+    if (g_alloc_countdown.load() >= 0 && g_alloc_countdown.fetch_sub(1) == 0) {
+        *p = nullptr;
+        return cudaErrorMemoryAllocation;
+    }
+    return cudaMalloc((void**)p, bytes);
+}
+}  // namespace
 
 using namespace lbm;
 
@@ -291,7 +318,7 @@ lbm_status ensure_stage(lbm_ctx* c, size_t bytes) {
     if (c->d_stage) cudaFree(c->d_stage);
     c->d_stage = nullptr;
     c->stage_bytes = 0;
-    LBM_CUDA(c, cudaMalloc(&c->d_stage, bytes), "allocating the staging buffer");
+    LBM_CUDA(c, dev_malloc(&c->d_stage, bytes), "allocating the staging buffer");
     c->stage_bytes = bytes;
     return LBM_OK;
 }
@@ -357,7 +384,7 @@ size_t level_bytes(const lbm_ctx* c) { return (size_t)(c->ny + 2) * (size_t)c->r
 lbm_status save_checkpoint(lbm_ctx* c, size_t k) {
     while (c->ck.size() <= k) {
         void* p = nullptr;
-        LBM_CUDA(c, cudaMalloc(&p, level_bytes(c)), "allocating a checkpoint");
+        LBM_CUDA(c, dev_malloc(&p, level_bytes(c)), "allocating a checkpoint");
         c->ck.push_back(p);
     }
     LBM_CUDA(c, cudaMemcpyAsync(c->ck[k], c->f[c->cur], level_bytes(c), cudaMemcpyDeviceToDevice, c->stream),
@@ -370,7 +397,7 @@ lbm_status ensure_astage(lbm_ctx* c, size_t bytes) {
     cudaFree(c->d_astage);
     c->d_astage = nullptr;
     c->astage_bytes = 0;
-    LBM_CUDA(c, cudaMalloc(&c->d_astage, bytes), "allocating the adjoint staging buffer");
+    LBM_CUDA(c, dev_malloc(&c->d_astage, bytes), "allocating the adjoint staging buffer");
     c->astage_bytes = bytes;
     return LBM_OK;
 }
@@ -453,8 +480,8 @@ extern "C" lbm_status lbm_probe_tile_copy(int nx, int ny, int reps, double* gbs)
     cudaEvent_t e0 = nullptr, e1 = nullptr;
     lbm_status r = LBM_OK;
     CUtensorMap m[2];
-    if (cudaMalloc(&f[0], bytes) != cudaSuccess || cudaMalloc(&f[1], bytes) != cudaSuccess ||
-        cudaMalloc((void**)&status, sizeof(unsigned)) != cudaSuccess) {
+    if (dev_malloc(&f[0], bytes) != cudaSuccess || dev_malloc(&f[1], bytes) != cudaSuccess ||
+        dev_malloc((void**)&status, sizeof(unsigned)) != cudaSuccess) {
         r = LBM_E_NOMEM;
     } else if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess ||
                cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess ||
@@ -537,12 +564,12 @@ lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx
     c->gf = build_grid<float>(*c, c->md);
     const size_t fbytes = level_bytes(c);
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = cudaMalloc(&c->f[k], fbytes);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_status, sizeof(unsigned));
+    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = dev_malloc(&c->f[k], fbytes);
+    if (e == cudaSuccess) e = dev_malloc((void**)&c->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_status, sizeof(unsigned));
     const int np = c->prec == LBM_FP64 ? conservation_partials(c->gd) : conservation_partials(c->gf);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_partials, sizeof(double) * 4 * np);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&c->d_sums, sizeof(double) * 4);
+    if (e == cudaSuccess) e = dev_malloc((void**)&c->d_partials, sizeof(double) * 4 * np);
+    if (e == cudaSuccess) e = dev_malloc((void**)&c->d_sums, sizeof(double) * 4);
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_sums, sizeof(double) * 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, fbytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[1], 0, fbytes, c->stream);
@@ -583,6 +610,7 @@ void lbm_destroy(lbm_ctx* c) {
 }
 
 lbm_status lbm_init(lbm_ctx* c, const void* rho, const void* ux, const void* uy, const void* T) {
+    NvtxRange nvtx_range("lbm_init");
     lbm_status s = enter(c);
     if (s != LBM_OK) return s;
     if (!rho || !ux || !uy || !T) return fail(c, LBM_E_INVAL, "lbm_init: fields must not be NULL");
@@ -611,6 +639,7 @@ lbm_status lbm_init(lbm_ctx* c, const void* rho, const void* ux, const void* uy,
 }
 
 lbm_status lbm_step(lbm_ctx* c, int n) {
+    NvtxRange nvtx_range("lbm_step");
     lbm_status s = enter(c);
     if (s != LBM_OK) return s;
     if (n < 0) return fail(c, LBM_E_INVAL, "lbm_step: n must be >= 0");
@@ -636,6 +665,7 @@ lbm_status lbm_step(lbm_ctx* c, int n) {
 }
 
 lbm_status lbm_moments(lbm_ctx* c, void* rho, void* ux, void* uy, void* T) {
+    NvtxRange nvtx_range("lbm_moments");
     lbm_status s = enter(c);
     if (s != LBM_OK) return s;
     if (!c->ready) return fail(c, LBM_E_STATE, "lbm_moments before lbm_init");
@@ -664,6 +694,7 @@ lbm_status lbm_moments(lbm_ctx* c, void* rho, void* ux, void* uy, void* T) {
 }
 
 lbm_status lbm_conservation(lbm_ctx* c, double out[4]) {
+    NvtxRange nvtx_range("lbm_conservation");
     lbm_status s = enter(c);
     if (s != LBM_OK) return s;
     if (!out) return fail(c, LBM_E_INVAL, "lbm_conservation: out must not be NULL");
@@ -747,6 +778,7 @@ lbm_status lbm_set_f(lbm_ctx* c, const void* src, long long step) {
 long long lbm_step_count(const lbm_ctx* c) { return c ? c->step : -1; }
 
 lbm_status lbm_record(lbm_ctx* c, int every) {
+    NvtxRange nvtx_range("lbm_record");
     lbm_status s = enter(c);
     if (s != LBM_OK) return s;
     if (every < 0) return fail(c, LBM_E_INVAL, "lbm_record: every must be >= 0");
@@ -759,6 +791,7 @@ lbm_status lbm_record(lbm_ctx* c, int every) {
 
 lbm_status lbm_adjoint_seed(lbm_ctx* c, const void* qr, const void* qx, const void* qy, const void* qT,
                             void* abar) {
+    NvtxRange nvtx_range("lbm_adjoint_seed");
     lbm_status s = enter(c);
     if (s != LBM_OK) return s;
     if (!abar) return fail(c, LBM_E_INVAL, "lbm_adjoint_seed: abar must not be NULL");
@@ -794,6 +827,7 @@ lbm_status lbm_adjoint_seed(lbm_ctx* c, const void* qr, const void* qx, const vo
 }
 
 lbm_status lbm_adjoint_step(lbm_ctx* c, int n, void* abar, double* dL_dtau) {
+    NvtxRange nvtx_range("lbm_adjoint_step");
     lbm_status s = enter(c);
     if (s != LBM_OK) return s;
     if (!abar || n < 0) return fail(c, LBM_E_INVAL, "lbm_adjoint_step: abar must not be NULL, n >= 0");
@@ -808,7 +842,7 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, int n, void* abar, double* dL_dtau) {
     adjoint_tile_boxes(&abx, &aby, &afx, &afy);
     for (int k = 0; k < 2; ++k)
         if (!c->adj[k]) {
-            LBM_CUDA(c, cudaMalloc(&c->adj[k], lb), "allocating adjoint levels");
+            LBM_CUDA(c, dev_malloc(&c->adj[k], lb), "allocating adjoint levels");
             LBM_CUDA(c, cudaMemsetAsync(c->adj[k], 0, lb, c->stream), "clearing adjoint levels");
             if (k == 1)
                 c->adj_tmaps_ok = fp32 && make_tmap_box(&c->adj_tmap[0], c->adj[0], *c, abx, aby) &&
@@ -816,7 +850,7 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, int n, void* abar, double* dL_dtau) {
         }
     while ((int)c->seg.size() < c->ck_every) {
         void* p = nullptr;
-        LBM_CUDA(c, cudaMalloc(&p, lb), "allocating segment levels");
+        LBM_CUDA(c, dev_malloc(&p, lb), "allocating segment levels");
         c->seg.push_back(p);
         CUtensorMap mf{}, ms{};
         if (c->adj_tmaps_ok && !(make_tmap_box(&mf, p, *c, afx, afy) && make_tmap(&ms, p, *c)))
@@ -832,7 +866,7 @@ lbm_status lbm_adjoint_step(lbm_ctx* c, int n, void* abar, double* dL_dtau) {
         cudaFreeHost(c->h_taup);
         c->d_taup = nullptr;
         c->h_taup = nullptr;
-        LBM_CUDA(c, cudaMalloc((void**)&c->d_taup, sizeof(double) * np), "allocating tau partials");
+        LBM_CUDA(c, dev_malloc((void**)&c->d_taup, sizeof(double) * np), "allocating tau partials");
         LBM_CUDA(c, cudaMallocHost((void**)&c->h_taup, sizeof(double) * np), "allocating tau partials");
         c->ntaup = np;
     }
@@ -996,6 +1030,7 @@ lbm_status lbm_get_launch(const lbm_ctx* c, lbm_launch* l) {
 }
 
 lbm_status lbm_autotune(lbm_ctx* c, int steps, lbm_launch* best, double* ms, int* n_candidates) {
+    NvtxRange nvtx_range("lbm_autotune");
     lbm_status s = enter(c);
     if (s != LBM_OK) return s;
     if (steps < 1) return fail(c, LBM_E_INVAL, "lbm_autotune: steps must be >= 1");
@@ -1352,12 +1387,12 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
                 return bfail(nullptr, LBM_E_CUDA, "lbm_batch_create: tensor maps unavailable on this driver");
             }
     }
-    cudaError_t e = cudaMalloc((void**)&b->d_probs, sizeof(BatchProb) * nprob);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_tiles, sizeof(int4) * tiles.size());
-    if (e == cudaSuccess && b->tb_ok) e = cudaMalloc((void**)&b->d_segs, sizeof(int4) * segs.size());
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_level, sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_bar, 2 * sizeof(unsigned));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_status, sizeof(unsigned));
+    cudaError_t e = dev_malloc((void**)&b->d_probs, sizeof(BatchProb) * nprob);
+    if (e == cudaSuccess) e = dev_malloc((void**)&b->d_tiles, sizeof(int4) * tiles.size());
+    if (e == cudaSuccess && b->tb_ok) e = dev_malloc((void**)&b->d_segs, sizeof(int4) * segs.size());
+    if (e == cudaSuccess) e = dev_malloc((void**)&b->d_level, sizeof(long long));
+    if (e == cudaSuccess) e = dev_malloc((void**)&b->d_bar, 2 * sizeof(unsigned));
+    if (e == cudaSuccess) e = dev_malloc((void**)&b->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&b->h_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->gstream, cudaStreamNonBlocking);
     if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming);
@@ -1384,11 +1419,11 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
                            : prec == LBM_FP32_CONS ? batch_max_grid<T_CONS>(npt)
                                                    : batch_max_grid<T_INT32>(npt);
     b->nbr_cap = b->max_grid[1] > b->max_grid[2] ? b->max_grid[1] : b->max_grid[2];
-    e = cudaMalloc((void**)&b->d_nbr, sizeof(int) * (size_t)b->nbr_cap * kBatchMaxNbr);
+    e = dev_malloc((void**)&b->d_nbr, sizeof(int) * (size_t)b->nbr_cap * kBatchMaxNbr);
     // one counter per CTA, and one more (index nbr_cap) that no CTA ever
     // publishes to (lbm_batch_plant_stall)
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_done, sizeof(unsigned long long) * (size_t)(b->nbr_cap + 1));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_epoch, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = dev_malloc((void**)&b->d_done, sizeof(unsigned long long) * (size_t)(b->nbr_cap + 1));
+    if (e == cudaSuccess) e = dev_malloc((void**)&b->d_epoch, sizeof(unsigned long long));
     if (e == cudaSuccess) e = cudaMemset(b->d_done, 0, sizeof(unsigned long long) * (size_t)(b->nbr_cap + 1));
     if (e == cudaSuccess) e = cudaMemset(b->d_epoch, 0, sizeof(unsigned long long));
     if (e != cudaSuccess) {
@@ -1432,6 +1467,7 @@ lbm_status lbm_batch_init(lbm_batch* b, const void* const* rho, const void* cons
 }
 
 lbm_status lbm_batch_step(lbm_batch* b, int n) {
+    NvtxRange nvtx_range("lbm_batch_step");
     if (!b) return bfail(nullptr, LBM_E_INVAL, "NULL batch");
     if (n < 0) return bfail(b, LBM_E_INVAL, "lbm_batch_step: n must be >= 0");
     if (!b->ready) return bfail(b, LBM_E_STATE, "lbm_batch_step before lbm_batch_init");
@@ -1554,6 +1590,7 @@ extern "C" {
 
 lbm_status lbm_vn_scan(const lbm_vn_case* cases, int ncases, const int* dirs, int ndirs, int nk,
                        double* radius, double* growth, void* stream) {
+    NvtxRange nvtx_range("lbm_vn_scan");
     if (ncases < 0) return fail(nullptr, LBM_E_INVAL, "ncases must be >= 0");
     if (ncases == 0) return LBM_OK;
     if (!cases || !dirs) return fail(nullptr, LBM_E_INVAL, "cases and dirs must not be NULL");
@@ -1650,6 +1687,11 @@ lbm_status lbm_batch_set_launch(lbm_batch* b, const lbm_batch_launch* l) {
     return LBM_OK;
 }
 
+lbm_status lbm_inject_alloc_failure(long long after) {
+    g_alloc_countdown.store(after < 0 ? -1 : after);
+    return LBM_OK;
+}
+
 lbm_status lbm_batch_set_wait_limit(double seconds) {
     if (!(seconds > 0.0) || seconds > 60.0) return LBM_E_INVAL;
     int dev = 0, khz = 0;
@@ -1702,6 +1744,7 @@ lbm_status lbm_batch_get_launch(const lbm_batch* b, lbm_batch_launch* l) {
 }
 
 lbm_status lbm_batch_autotune(lbm_batch* b, int steps, lbm_batch_launch* best, double* ms, int* n_candidates) {
+    NvtxRange nvtx_range("lbm_batch_autotune");
     if (!b) return bfail(nullptr, LBM_E_INVAL, "NULL batch");
     if (steps < 1) return bfail(b, LBM_E_INVAL, "lbm_batch_autotune: steps must be >= 1");
     if (!b->ready) return bfail(b, LBM_E_STATE, "lbm_batch_autotune before lbm_batch_init");
@@ -1726,9 +1769,9 @@ lbm_status lbm_batch_autotune(lbm_batch* b, int steps, lbm_batch_launch* best, d
     unsigned char* save = nullptr;
     long long* d_lsave = nullptr;
     unsigned* d_ssave = nullptr;
-    cudaError_t e = cudaMalloc((void**)&save, total);
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_lsave, sizeof(long long));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&d_ssave, sizeof(unsigned));
+    cudaError_t e = dev_malloc((void**)&save, total);
+    if (e == cudaSuccess) e = dev_malloc((void**)&d_lsave, sizeof(long long));
+    if (e == cudaSuccess) e = dev_malloc((void**)&d_ssave, sizeof(unsigned));
     size_t off = 0;
     for (lbm_ctx* c : b->ctx) {
         if (e == cudaSuccess)

@@ -32,7 +32,8 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init", "lbm_step"
            "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_last_error", "lbm_batch_init",
            "lbm_batch_step", "lbm_batch_sync", "lbm_batch_problem", "lbm_batch_info",
            "lbm_probe_rates", "lbm_vn_scan", "lbm_batch_set_launch", "lbm_batch_get_launch",
-           "lbm_batch_autotune", "lbm_probe_tile_copy", "lbm_batch_set_wait_limit", "lbm_batch_plant_stall")
+           "lbm_batch_autotune", "lbm_probe_tile_copy", "lbm_batch_set_wait_limit", "lbm_batch_plant_stall",
+           "lbm_inject_alloc_failure")
 LBM_FLAG_NONPHYSICAL, LBM_FLAG_TIMEOUT, LBM_FLAG_T_NONPOSITIVE = 1, 2, 4
 
 
@@ -126,6 +127,7 @@ def load():
                                 ctypes.c_int),
         "lbm_batch_set_wait_limit": ([ctypes.c_double], ctypes.c_int),
         "lbm_batch_plant_stall": ([_VP, ctypes.c_int], ctypes.c_int),
+        "lbm_inject_alloc_failure": ([ctypes.c_longlong], ctypes.c_int),
         "lbm_batch_create": ([ctypes.c_int, ctypes.POINTER(lbm_problem), ctypes.c_int, _VP,
                               ctypes.POINTER(_VP)], ctypes.c_int),
         "lbm_batch_destroy": ([_VP], None),
@@ -431,6 +433,11 @@ def lbm_batch_set_wait_limit(seconds: float) -> None:
     st = load().lbm_batch_set_wait_limit(float(seconds))
     if st != LBM_OK:
         raise LbmError(st, "lbm_batch_set_wait_limit failed")
+
+
+def lbm_inject_alloc_failure(after: int) -> None:
+    """The library's device allocation after the next `after` ones fails (after < 0: off)."""
+    load().lbm_inject_alloc_failure(int(after))
 
 
 def lbm_batch_plant_stall(b, cta: int):
