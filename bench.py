@@ -411,26 +411,34 @@ def cpu_baseline(p, seconds, threads=None):
     threads = threads or (os.cpu_count() or 1)
     oracle.set_threads(threads)
     f = oracle.init(p, *W.initial_fields(p))
+    oracle.run(p, f, 1, 0)  # first step: starts the worker threads
     t0 = time.perf_counter()
-    oracle.run(p, f, 1, 0)
+    oracle.run(p, f, 1, 1)  # a warm step sizes the sample
     one = time.perf_counter() - t0
-    n = max(1, int(seconds / max(one, 1e-6)) - 1)
-    t0 = time.perf_counter()
-    oracle.run(p, f, n, 1)
-    el = time.perf_counter() - t0
+    # whole steps in chunks until about `seconds` of work is done
+    chunk = max(1, int(seconds / max(one, 1e-6) / 4))
+    n, el = 0, 0.0
+    while el < seconds:
+        t0 = time.perf_counter()
+        oracle.run(p, f, chunk, 2 + n)
+        el += time.perf_counter() - t0
+        n += chunk
     out = {"value": round(p.nodes * n / el / 1e9, 6), "unit": "GLUPS", "cores": threads,
            "kind": "oracle",
-           "sample": f"FP64 oracle on {p.name}, {n} whole steps (steps 1..{n}) in {el:.1f} s",
+           "sample": f"FP64 oracle on {p.name}, {n} whole steps (steps 2..{n + 1}) in {el:.1f} s",
            "cpu_model": cpu_model()}
     if threads > 1:  # the same oracle on one core, a few whole steps
         oracle.set_threads(1)
         f = oracle.init(p, *W.initial_fields(p))
-        m = max(1, int(min(seconds, 4.0) / max(one * threads, 1e-6)))
         t0 = time.perf_counter()
-        oracle.run(p, f, m, 0)
+        oracle.run(p, f, 1, 0)
+        one1 = time.perf_counter() - t0
+        m = max(1, int(min(seconds, 4.0) / max(one1, 1e-6)))
+        t0 = time.perf_counter()
+        oracle.run(p, f, m, 1)
         el1 = time.perf_counter() - t0
         out["serial"] = {"value": round(p.nodes * m / el1 / 1e9, 6), "unit": "GLUPS", "cores": 1,
-                         "sample": f"{m} whole steps (steps 0..{m - 1}) in {el1:.1f} s"}
+                         "sample": f"{m} whole steps (steps 1..{m}) in {el1:.1f} s"}
         oracle.set_threads(threads)
     return out
 
