@@ -329,6 +329,39 @@ def test_every_launch_shape_gives_the_same_bits(prec, ny):
         assert np.array_equal(o, outs[0]), s
 
 
+DEGENERATE = RAGGED + [
+    (1, 9, (Side("periodic"),) * 4),
+    (9, 1, (Side("periodic"),) * 4),
+    (70, 1, (Side("outflow"), Side("outflow"), Side("periodic"), Side("periodic"))),
+    (1, 70, (Side("periodic"), Side("periodic"), Side("outflow"), Side("reflect"))),
+]
+
+
+@pytest.mark.parametrize("nx,ny,sides", DEGENERATE)
+def test_fp32_every_launch_shape_on_tiny_and_ragged_grids(nx, ny, sides):
+    """Grids of one node, one row or one column, and grids smaller than a
+    tile, with every boundary kind: every FP32 launch shape gives the same
+    bits, and the tile kernel stays within FP32 accuracy of the FP64
+    oracle."""
+    rng = np.random.Generator(np.random.PCG64(nx * 1000 + ny + 7))
+    p = W.uniform(nx, ny, (1.0, 0.0, 0.0, 1.0), dx=0.01, alpha=0.1, sides=sides, steps=40)
+    p = p.with_(tau=p.dt / 0.7)
+    fields = (1.0 + 0.3 * rng.random((ny, nx)), 0.5 * rng.standard_normal((ny, nx)),
+              0.5 * rng.standard_normal((ny, nx)), 1.0 + 0.3 * rng.random((ny, nx)))
+    outs = []
+    for shape in SHAPES:
+        with lbm.Lattice(p, "fp32_cons") as lat:
+            lbm.lbm_set_launch(lat.ctx, *shape)
+            lat.init(*fields).step(p.steps)
+            lat.sync()
+            outs.append(lat.get_f().cpu().numpy())
+    for shape, o in zip(SHAPES[1:], outs[1:]):
+        assert np.array_equal(o, outs[0]), shape
+    ref = oracle_run(p, fields=fields)[0]
+    err = max_rel(gpu_run(p, "fp32_cons", fields=fields), ref)
+    assert max(err.values()) <= 1e-4, err
+
+
 @pytest.mark.parametrize("shape", [(3, 0, 0, 0), (1, 128, 4, 0), (2, 4, 0, 0), (2, 2, 0, 0)])
 def test_fp32_kernels_match_oracle_on_ragged_grid(shape):
     p = W.dmr(37).with_(nx=151, steps=120)
