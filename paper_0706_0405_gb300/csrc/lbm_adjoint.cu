@@ -264,9 +264,21 @@ __global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS)
     // population strides PA, PF and row strides RA, RF
     constexpr int PA = kAdjBoxX, RA = 9 * kAdjBoxX, PF = kAdjTX, RF = 9 * kAdjTX;
     float wsum = 0.0f;  // this warp's tau terms, tile by tile in a fixed order (FP32 over a few tiles)
+    // tile coordinates walked incrementally (t advances by gridDim.x): no
+    // integer division per tile
+    const int step_x = (int)gridDim.x % tiles_x, step_y = (int)gridDim.x / tiles_x;
+    int tile_x = (int)blockIdx.x % tiles_x, tile_y = (int)blockIdx.x / tiles_x;
     for (int k = 0;; ++k) {
         const int t = blockIdx.x + k * gridDim.x;
         if (t >= ntiles) break;
+        if (k > 0) {
+            tile_x += step_x;
+            tile_y += step_y;
+            if (tile_x >= tiles_x) {
+                tile_x -= tiles_x;
+                ++tile_y;
+            }
+        }
         if (tid == 0 && !wait(k)) abort_flag = 1;
         __syncthreads();
         if (abort_flag) {
@@ -281,7 +293,7 @@ __global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS)
         }
         float tn = 0.0f;
         if constexpr (kAdjNpt == 1) {
-            const int ix = (t % tiles_x) * kAdjTX + tx, iy = (t / tiles_x) * kAdjTY + ty;
+            const int ix = tile_x * kAdjTX + tx, iy = tile_y * kAdjTY + ty;
             if (ix < G.nx && iy < G.ny) {
                 const float* sA = stage0 + (k & 1) * kAdjStageFloats + (ty + 1) * RA + (tx + 4);
                 const float* sF = stage0 + (k & 1) * kAdjStageFloats + kAdjAPad + ty * RF + tx;
@@ -309,7 +321,7 @@ __global__ void __launch_bounds__(kAdjThreads, LBM_ADJ_MIN_BLOCKS)
                 for (int j = 0; j < 9; ++j) abar[j * pl + c] = o[j];
             }
         } else {  // two x-adjacent nodes per thread: 8-byte shared loads and stores
-            const int ix0 = (t % tiles_x) * kAdjTX + 2 * tx, iy = (t / tiles_x) * kAdjTY + ty;
+            const int ix0 = tile_x * kAdjTX + 2 * tx, iy = tile_y * kAdjTY + ty;
             if (ix0 < G.nx && iy < G.ny) {
                 const int nvalid = min(2, G.nx - ix0);
                 const float* sA = stage0 + (k & 1) * kAdjStageFloats + (ty + 1) * RA + (2 * tx + 4);
