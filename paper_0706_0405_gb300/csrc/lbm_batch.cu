@@ -1,12 +1,15 @@
 // lbm_batch.cu -- many independent problems (each its own grid, constants and
 // boundary kinds) advanced by one persistent cooperative launch: every CTA
-// walks a contiguous share of the (problem, 64 x 4 tile) list per step, and a
-// bounded grid barrier separates the steps.  Each tile and its halo (72 x 6
-// x 9 floats) arrive in shared memory by one tiled tensor copy through the
-// problem's own tensor map, double-buffered so that the next tile of the
-// CTA's share is in flight while the current one is computed; every thread
-// then updates one node with the same per-node arithmetic as the single-grid
-// kernels, so each problem's levels are bit-identical to stepping it alone.
+// walks its share of the (problem, 64 x 4 tile) list per step, and a CTA
+// starts a step once the CTAs owning the tiles next to its own have finished
+// the previous one (bounded waits; a grid barrier where the neighbour lists
+// would be too long).  Each tile and its halo (72 x 6 x 9 floats, or the
+// 72 x 4 x 9 interior rows of a problem that wraps in y inside one tile row)
+// arrive in shared memory by one tiled tensor copy through the problem's own
+// tensor map, double-buffered so that the next tile of the CTA's share is in
+// flight while the current one is computed; every thread then updates one or
+// two nodes with the same per-node arithmetic as the single-grid kernels, so
+// each problem's levels are bit-identical to stepping it alone.
 #include "lbm_launch.h"
 #include "lbm_ptx.cuh"
 
