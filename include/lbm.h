@@ -310,8 +310,10 @@ lbm_status lbm_conservation_noalloc(const void* f, int nx, int ny, lbm_precision
  * Many independent problems (each with its own grid, constants and boundary
  * kinds) advanced together by one persistent cooperative kernel launch per
  * lbm_batch_step call: every CTA walks a contiguous share of the list of
- * (problem, 64 x 4 node tile) pairs each step and a bounded grid barrier
- * separates the steps (LBM_E_TIMEOUT if it gives up).  The launch is captured
+ * (problem, 64 x 4 node tile) pairs each step, and starts a step once the
+ * CTAs owning the tiles next to its own have finished the previous one
+ * (bounded waits, LBM_E_TIMEOUT if one gives up; see lbm_batch_plant_stall
+ * below).  The launch is captured
  * once per step count into a CUDA graph on a stream private to the batch and
  * replayed there, ordered after the batch's stream by events (so the legacy
  * default stream works too); if capture fails the launch runs directly.  The per-node
