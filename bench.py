@@ -279,6 +279,7 @@ def run_ours(args, world, dist):
                      "note": f"per call: {nbytes} B up (4 fields), {nbytes} B down (moments), "
                              f"{args.steps} steps, host wall clock"}
     if args.extras:
+        args.headline_glups = glups
         result.update(extras(args, p, fields, stream))
     return result, p
 
@@ -309,6 +310,8 @@ def extras(args, p, fields, stream):
                                "flops_per_node": FP64_FLOPS_PER_NODE}
         prec_rows[prec] = row
     out["precisions"] = prec_rows
+    if "fp64" in prec_rows:  # the FP32 path against the plain FP64 step on the same grid
+        out["precisions"]["headline_over_fp64"] = round(args.headline_glups / prec_rows["fp64"]["GLUPS"], 2)
     out["device_rates"] = {"fp64_tflops": round(fp64_tf, 3), "fp32_tflops": round(fp32_tf, 2)}
 
     # adjoint / forward on the Mach-3 2048 x 256 tube, 1000 steps, checkpoint every 50
@@ -327,10 +330,16 @@ def extras(args, p, fields, stream):
         t0 = time.perf_counter()
         lbm.lbm_adjoint_step(la.ctx, q.steps, abar)  # synchronises
         adj = time.perf_counter() - t0
+    # the plain FP64 forward step on the same tube, for the ratio against it
+    with lbm.Lattice(q, "fp64") as l64:
+        l64.init(*qf)
+        fwd64 = plain_steps(l64, q.steps, stream)
+        l64.sync()
     out["adjoint"] = {"workload": q.name, "steps": q.steps, "checkpoint_every": 50,
                       "forward_s": round(fwd_plain, 5), "forward_recording_s": round(fwd_rec, 5),
                       "adjoint_s": round(adj, 5), "adjoint_over_forward": round(adj / fwd_plain, 3),
-                      "ideal_ratio_by_traffic": 2.5}
+                      "ideal_ratio_by_traffic": 2.5, "forward_fp64_s": round(fwd64, 5),
+                      "adjoint_over_fp64_forward": round(adj / fwd64, 3)}
 
     # 256 tubes in one persistent launch vs 256 separate sequences of launches
     probs = W.batch_riemann()
