@@ -243,6 +243,11 @@ def run_ours(args, world, dist):
         "config": {"workload": f"dmr_{p.nx}x{p.ny}", "nx": p.nx, "ny": p.ny,
                    "precision": args.precision, "c1_c2_eta0": [p.c1, p.c2, p.eta0],
                    "alpha": round(p.alpha, 6), "launch": list(launch),
+                   "precision_note": ("FP32 storage and arithmetic; the temperature is kept by a "
+                                      "moment-exact relaxation, which matches the FP64 and double-float "
+                                      "temperature recovery modes (fp32_t64, fp32_tdf, timed under "
+                                      "'precisions') in accuracy on every workload; FP64 is used for the "
+                                      "conservation sums"),
                    "l2": "inputs larger than L2 (152 MB per level, two levels)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
