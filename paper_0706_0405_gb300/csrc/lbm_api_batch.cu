@@ -2,6 +2,7 @@
 // problems advanced by one persistent launch, its launch shape and
 // autotuner, the neighbour lists that order its steps, and its test hooks.
 #include "lbm_api_internal.h"
+#include "lbm_batch_plan.h"
 
 // ------------------------------------------------------------------ batch
 struct lbm_batch {
@@ -57,37 +58,20 @@ lbm_status bfail(lbm_batch* b, lbm_status s, const std::string& msg) {
 // tiles in x or y, across periodic sides too.  False if some CTA has more
 // than kBatchMaxNbr.
 bool batch_neighbour_lists(const lbm_batch* b, int grid, std::vector<int>& out) {
-    out.assign((size_t)grid * kBatchMaxNbr, -1);
-    std::vector<int> cnt(grid, 0);
-    auto add = [&](int c, int n) {
-        if (n == c) return true;
-        for (int j = 0; j < cnt[c]; ++j)
-            if (out[(size_t)c * kBatchMaxNbr + j] == n) return true;
-        if (cnt[c] == kBatchMaxNbr) return false;
-        out[(size_t)c * kBatchMaxNbr + cnt[c]++] = n;
-        return true;
-    };
     int tw = 0, th = 0;
     batch_tile_dims(&tw, &th);
-    for (int t = 0; t < b->ntiles; ++t) {
-        const int4 T = b->tiles[t];
-        const int p = T.x, tx = b->tiles_x[p], ty = b->tiles_y[p];
-        const int ix = T.y / tw, iy = T.z / th, c = batch_tile_owner(t, b->ntiles, grid);
-        const int nb[4][2] = {{ix - 1, iy}, {ix + 1, iy}, {ix, iy - 1}, {ix, iy + 1}};
-        for (const auto& q : nb) {
-            int jx = q[0], jy = q[1];
-            if (jx < 0 || jx >= tx) {
-                if (!b->periodic_x[p]) continue;
-                jx = (jx + tx) % tx;
-            }
-            if (jy < 0 || jy >= ty) {
-                if (!b->periodic_y[p]) continue;
-                jy = (jy + ty) % ty;
-            }
-            if (!add(c, batch_tile_owner(b->tile_base[p] + jy * tx + jx, b->ntiles, grid))) return false;
-        }
+    const int n = b->ntiles;
+    std::vector<int> tp((size_t)n), tix((size_t)n), tiy((size_t)n);
+    for (int t = 0; t < n; ++t) {
+        tp[(size_t)t] = b->tiles[(size_t)t].x;
+        tix[(size_t)t] = b->tiles[(size_t)t].y / tw;
+        tiy[(size_t)t] = b->tiles[(size_t)t].z / th;
     }
-    return true;
+    std::vector<unsigned char> px(b->periodic_x.begin(), b->periodic_x.end()),
+        py(b->periodic_y.begin(), b->periodic_y.end());
+    return batch_plan_neighbours(n, tp.data(), tix.data(), tiy.data(), b->tiles_x.data(), b->tiles_y.data(),
+                                 b->tile_base.data(), px.data(), py.data(), grid,
+                                 [&](int t) { return batch_tile_owner(t, n, grid); }, kBatchMaxNbr, out);
 }
 
 // Make the neighbour lists match the current grid (outside graph capture:
