@@ -239,3 +239,53 @@ def test_mach3_gradient_wrt_left_and_right_states_against_finite_differences():
         fm = [np.ascontiguousarray(a) for a in _fields_from_states(p, sm, z, 0.01, np)]
         fd = (_loss(p, fp, target) - _loss(p, fm, target)) / (2 * h)
         assert st[k].grad.item() == pytest.approx(fd, rel=1e-4, abs=1e-8 * abs(loss.item())), k
+
+
+TINY = [
+    (1, 1, (Side("periodic"),) * 4),
+    (1, 9, (Side("periodic"), Side("periodic"), Side("outflow"), Side("reflect"))),
+    (9, 1, (Side("outflow"), Side("reflect"), Side("periodic"), Side("periodic"))),
+    (70, 3, MIXED),
+    (3, 70, (Side("reflect"),) * 4),
+]
+
+
+@pytest.mark.parametrize("nx,ny,sides", TINY)
+def test_adjoint_on_one_node_one_row_and_one_column_grids(nx, ny, sides):
+    """One adjoint step on grids of one node, one column, one row and thinner
+    than a tile: FP64 against the oracle adjoint to 1e-12, and the FP32 tile
+    and thread-per-node adjoint kernels against it to FP32 accuracy."""
+    rng = np.random.Generator(np.random.PCG64(nx * 100 + ny))
+    p = W.uniform(nx, ny, (1.0, 0.0, 0.0, 1.0), dx=0.1, alpha=0.2, sides=sides, lam_scale=2.0)
+    p = p.with_(tau=p.dt / 0.8)
+    f0 = _random_state(p, rng)
+    w = rng.standard_normal((9, p.ny, p.nx))
+    n = 3
+    state = oracle.empty_state(p)
+    oracle.interior(state)[:] = f0
+    want, want_tau = oracle.adjoint_step(p, state, n, np.pad(w, ((0, 0), (1, 1), (1, 1))))
+    wi = oracle.interior(want)
+    scale = np.max(np.abs(wi))
+    with lbm.Lattice(p, "fp64") as lat:
+        lat.set_f(f0, n)
+        lbm.lbm_record(lat.ctx, 1)
+        lat.step(1)
+        abar = w.copy()
+        dtau = lbm.lbm_adjoint_step(lat.ctx, 1, abar)
+    assert np.max(np.abs(abar - wi)) <= 1e-12 * scale
+    assert dtau == pytest.approx(want_tau, rel=1e-10, abs=1e-12 * abs(want_tau) + 1e-14)
+    # FP32 against the oracle run on the FP32-rounded inputs
+    state32 = oracle.empty_state(p)
+    oracle.interior(state32)[:] = f0.astype(np.float32).astype(np.float64)
+    want32, _ = oracle.adjoint_step(p, state32, n, np.pad(w.astype(np.float32).astype(np.float64),
+                                                          ((0, 0), (1, 1), (1, 1))))
+    wi32 = oracle.interior(want32)
+    for variant in (3, 0):
+        with lbm.Lattice(p, "fp32_cons") as lat:
+            lbm.lbm_set_launch(lat.ctx, variant)
+            lat.set_f(f0.astype(np.float32), n)
+            lbm.lbm_record(lat.ctx, 1)
+            lat.step(1)
+            abar = w.astype(np.float32)
+            lbm.lbm_adjoint_step(lat.ctx, 1, abar)
+        assert np.max(np.abs(abar.astype(np.float64) - wi32)) <= 2e-5 * scale, variant

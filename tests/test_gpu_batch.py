@@ -192,3 +192,24 @@ def test_a_neighbour_that_never_finishes_times_out_and_the_batch_recovers():
             lat.init(*fl).step(10)
             want = lat.get_f().cpu().numpy()
         assert np.array_equal(g, want), p.name
+
+
+def test_one_column_and_one_node_problems_in_a_batch():
+    """Problems one node wide, one node in all, and a few nodes in each
+    direction, periodic or not, stepped together: each equals the problem
+    stepped alone, bit for bit."""
+    P, O, R = W.Side("periodic"), W.Side("outflow"), W.Side("reflect")
+    st = (1.0, 0.1, 0.05, 1.0)
+    probs = [W.uniform(1, 1, st, sides=(P, P, P, P)), W.uniform(1, 6, st, sides=(P, P, O, R)),
+             W.uniform(2, 2, st, sides=(O, O, P, P)), W.uniform(3, 5, st, sides=(R, R, R, R)),
+             W.uniform(65, 4, st, sides=(O, O, P, P))]
+    fields = [W.initial_fields(p, seed=10 + k, sigma=0.01) for k, p in enumerate(probs)]
+    with lbm.Batch(probs, "fp32_cons") as b:
+        b.init(fields).step(17).step(13)
+        b.sync()
+        got = [b.get_f(k).cpu().numpy() for k in range(len(probs))]
+    for p, fl, g in zip(probs, fields, got):
+        with lbm.Lattice(p, "fp32_cons") as lat:
+            lat.init(*fl).step(30)
+            want = lat.get_f().cpu().numpy()
+        assert np.array_equal(g, want), p.name
