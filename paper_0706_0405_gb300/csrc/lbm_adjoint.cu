@@ -459,15 +459,8 @@ cudaError_t launch_adjoint_tile(const CUtensorMap& tmapA, const CUtensorMap& tma
     if (e != cudaSuccess) return e;
     const int tiles_x = (G.nx + kAdjTX - 1) / kAdjTX;
     const int ntiles = tiles_x * ((G.ny + kAdjTY - 1) / kAdjTY);
-    static int full_wave = 0;
-    if (full_wave == 0) {
-        int dev = 0, sms = 0, per_sm = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kAdjThreads, kAdjSmem);
-        full_wave = sms * (per_sm > 0 ? per_sm : 1);
-    }
-    const int grid = ntiles < full_wave ? ntiles : full_wave;
+    const int wave = full_wave<k_adjoint_tile<TM>>(kAdjThreads, kAdjSmem);
+    const int grid = ntiles < wave ? ntiles : wave;
     kern<<<grid, kAdjThreads, kAdjSmem, st>>>(tmapA, tmapF, abar, M, G, level, taup, tiles_x, ntiles, status);
     return cudaGetLastError();
 }

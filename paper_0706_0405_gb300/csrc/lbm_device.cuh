@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
 
 namespace lbm {
 
@@ -98,8 +99,19 @@ __host__ __device__ constexpr int mirror_y(int i) {
 // variants then produce the same bits for the same level.
 __device__ __forceinline__ float add_(float a, float b) { return __fadd_rn(a, b); }
 __device__ __forceinline__ float sub_(float a, float b) { return __fsub_rn(a, b); }
-__device__ __forceinline__ float mul_(float a, float b) { return __fmul_rn(a, b); }
 __device__ __forceinline__ float fma_(float a, float b, float c) { return __fmaf_rn(a, b, c); }
+// FP32 products flush subnormal operands and results to zero (.ftz), in the
+// scalar and the packed (F2) form alike: the packed product is only kept
+// apart from the add or subtract that consumes it in its .ftz form (the code
+// generator fuses a plain packed product into a following packed add or
+// subtract, which changes the rounding), and the scalar one follows it so
+// that both forms give the same bits.  Products this small never occur in
+// the populations or moments of any workload.
+__device__ __forceinline__ float mul_(float a, float b) {
+    float r;
+    asm("mul.rn.ftz.f32 %0, %1, %2;" : "=f"(r) : "f"(a), "f"(b));
+    return r;
+}
 // FP32: the hardware approximate reciprocal (PTX rcp.approx.ftz.f32, about
 // 1 ulp), issued as one instruction so that every kernel gets the same bits
 // whatever it does with the result; the error of the FP32 modes is set by
@@ -117,6 +129,68 @@ __device__ __forceinline__ double rcp_(double a) { return __drcp_rn(a); }
 __device__ __forceinline__ float neg_(float a) { return -a; }
 __device__ __forceinline__ double neg_(double a) { return -a; }
 
+// ------------------------------------------------- packed pairs of FP32
+// F2 holds the same quantity of two nodes in one 64-bit register pair; its
+// operations are the packed FP32x2 instructions of sm_100+ (add / sub / fma
+// .rn.f32x2, mul .rn.ftz.f32x2), which round each lane exactly as the scalar
+// operation does, so a kernel that updates two nodes with them produces the
+// scalar kernels' bits with half the arithmetic instructions.  A scalar
+// operand is broadcast to both lanes.
+struct F2 {
+    unsigned long long v;
+};
+__device__ __forceinline__ F2 pair(float a, float b) {
+    F2 r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r.v) : "f"(a), "f"(b));
+    return r;
+}
+__device__ __forceinline__ F2 bcast(float a) { return pair(a, a); }
+__device__ __forceinline__ F2 bcast(F2 a) { return a; }
+__device__ __forceinline__ float2 lanes(F2 a) {
+    float2 r;
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(r.x), "=f"(r.y) : "l"(a.v));
+    return r;
+}
+__device__ __forceinline__ float lane0(F2 a) { return lanes(a).x; }
+__device__ __forceinline__ float lane1(F2 a) { return lanes(a).y; }
+__device__ __forceinline__ F2 add2_(F2 a, F2 b) {
+    F2 r;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 sub2_(F2 a, F2 b) {
+    F2 r;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 mul2_(F2 a, F2 b) {
+    F2 r;
+    asm("mul.rn.ftz.f32x2 %0, %1, %2;" : "=l"(r.v) : "l"(a.v), "l"(b.v));
+    return r;
+}
+__device__ __forceinline__ F2 fma2_(F2 a, F2 b, F2 c) {
+    F2 r;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r.v) : "l"(a.v), "l"(b.v), "l"(c.v));
+    return r;
+}
+template <typename A, typename B>
+constexpr bool any_pair = std::is_same<A, F2>::value || std::is_same<B, F2>::value;
+template <typename A, typename B, typename C>
+constexpr bool any_pair3 = any_pair<A, B> || std::is_same<C, F2>::value;
+
+template <typename A, typename B, std::enable_if_t<any_pair<A, B>, int> = 0>
+__device__ __forceinline__ F2 add_(A a, B b) { return add2_(bcast(a), bcast(b)); }
+template <typename A, typename B, std::enable_if_t<any_pair<A, B>, int> = 0>
+__device__ __forceinline__ F2 sub_(A a, B b) { return sub2_(bcast(a), bcast(b)); }
+template <typename A, typename B, std::enable_if_t<any_pair<A, B>, int> = 0>
+__device__ __forceinline__ F2 mul_(A a, B b) { return mul2_(bcast(a), bcast(b)); }
+template <typename A, typename B, typename C, std::enable_if_t<any_pair3<A, B, C>, int> = 0>
+__device__ __forceinline__ F2 fma_(A a, B b, C c) { return fma2_(bcast(a), bcast(b), bcast(c)); }
+// -a exactly, subnormals and signed zeros included (there is no packed
+// negation): -0 - a in each lane.
+__device__ __forceinline__ F2 neg_(F2 a) { return sub2_(bcast(-0.0f), a); }
+__device__ __forceinline__ F2 rcp_(F2 a) { return pair(rcp_(lane0(a)), rcp_(lane1(a))); }
+
 // Internal energy sum_i f_i w_i with the nine exact FP32 products summed in
 // FP64.
 __device__ __forceinline__ float int64_energy(const float (&f)[9], const float (&w)[9]) {
@@ -125,6 +199,30 @@ __device__ __forceinline__ float int64_energy(const float (&f)[9], const float (
     for (int i = 1; i < 9; ++i) acc = __fma_rn((double)f[i], (double)w[i], acc);
     return (float)acc;
 }
+// The same for two nodes: each lane's sum as above.
+__device__ __forceinline__ F2 int64_energy(const F2 (&f)[9], const F2 (&w)[9]) {
+    float a[9], b[9], v[9], u[9];
+#pragma unroll
+    for (int i = 0; i < 9; ++i) {
+        a[i] = lane0(f[i]);
+        b[i] = lane1(f[i]);
+        v[i] = lane0(w[i]);
+        u[i] = lane1(w[i]);
+    }
+    return pair(int64_energy(a, v), int64_energy(b, u));
+}
+
+// TwoSum (Knuth): s + e = a + b exactly, s = a + b rounded.
+template <typename V>
+__device__ __forceinline__ void two_sum(V a, V b, V& s, V& e) {
+    s = add_(a, b);
+    const V bb = sub_(s, a);
+    e = add_(sub_(a, sub_(s, bb)), sub_(b, bb));
+}
+
+#ifndef LBM_TDF_TREE
+#define LBM_TDF_TREE 0
+#endif
 
 // ---------------------------------------------------------------- moments
 // rho = sum f (Eq. e4), rho u = sum f v (Eq. e5), T from Eq. (e7).
@@ -160,7 +258,30 @@ __device__ __forceinline__ void moments(const V (&f)[9], const Model<S>& M, V& r
             for (int i = 1; i < 9; ++i) e = fma_(f[i], w[i], e);
         } else if constexpr (TM == T_INT64) {
             e = int64_energy(f, w);
-        } else {  // T_DF: exact products p_i + q_i summed by TwoSum (Knuth)
+        } else {  // T_DF: exact products p_i + q_i, double-float sum
+#if LBM_TDF_TREE
+            // the p_i summed by a tree of TwoSums (Knuth), depth 4; every
+            // product and sum error collected in lo
+            V p[9], q[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                p[i] = mul_(f[i], w[i]);
+                q[i] = fma_(f[i], w[i], neg_(p[i]));
+            }
+            V s01, e01, s23, e23, s45, e45, s67, e67, s03, e03, s47, e47, s07, e07, hi, e08;
+            two_sum(p[0], p[1], s01, e01);
+            two_sum(p[2], p[3], s23, e23);
+            two_sum(p[4], p[5], s45, e45);
+            two_sum(p[6], p[7], s67, e67);
+            two_sum(s01, s23, s03, e03);
+            two_sum(s45, s67, s47, e47);
+            two_sum(s03, s47, s07, e07);
+            two_sum(s07, p[8], hi, e08);
+            const V qa = add_(add_(add_(q[0], q[1]), add_(q[2], q[3])), add_(add_(q[4], q[5]), add_(q[6], q[7])));
+            const V ea = add_(add_(add_(e01, e23), add_(e45, e67)), add_(add_(e03, e47), add_(e07, e08)));
+            e = add_(hi, add_(add_(qa, q[8]), ea));
+#else
+            // sequentially: TwoSum (Knuth) of each p_i into hi, errors in lo
             V hi{}, lo{};  // +0 in every lane
 #pragma unroll
             for (int i = 0; i < 9; ++i) {
@@ -172,6 +293,7 @@ __device__ __forceinline__ void moments(const V (&f)[9], const Model<S>& M, V& r
                 hi = s;
             }
             e = add_(hi, lo);
+#endif
         }
         T = mul_(mul_(e, inv), M.inv_b);
     }

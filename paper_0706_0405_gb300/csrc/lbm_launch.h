@@ -4,23 +4,48 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "lbm_device.cuh"
 
 namespace lbm {
 
 // Raise a kernel's dynamic shared-memory limit once per device (the setting
 // persists; calling the runtime for it on every launch costs microseconds
-// per step on small grids).
+// per step on small grids).  Host threads may race here: the bit mask is
+// atomic and a repeated call is harmless.
 template <auto Kern>
 inline cudaError_t allow_smem(size_t bytes) {
-    static unsigned done = 0;  // per kernel: one bit per device ordinal < 32
+    static std::atomic<unsigned> done{0};  // per kernel: one bit per device ordinal < 32
     int dev = 0;
     cudaGetDevice(&dev);
-    const unsigned bit = dev < 32 ? 1u << dev : 0u;
-    if (bit && (done & bit)) return cudaSuccess;
+    const unsigned bit = dev >= 0 && dev < 32 ? 1u << dev : 0u;
+    if (bit && (done.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
     const cudaError_t e = cudaFuncSetAttribute(Kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e == cudaSuccess) done |= bit;
+    if (e == cudaSuccess) done.fetch_or(bit, std::memory_order_relaxed);
     return e;
+}
+
+// CTAs of one full wave of `Kern` on the current device: SMs x resident CTAs
+// per SM at `threads` threads and `smem` bytes of dynamic shared memory.
+// Cached per device ordinal (devices may differ in SM count); host threads
+// that race to fill an entry all store the same value.
+template <auto Kern>
+inline int full_wave(int threads, size_t smem) {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const bool cached = dev >= 0 && dev < 64;
+    if (cached) {
+        const int v = cache[dev].load(std::memory_order_relaxed);
+        if (v > 0) return v;
+    }
+    int sms = 0, per_sm = 0;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, Kern, threads, smem);
+    const int v = (sms > 0 ? sms : 1) * (per_sm > 0 ? per_sm : 1);
+    if (cached) cache[dev].store(v, std::memory_order_relaxed);
+    return v;
 }
 
 // Kernel variant and launch shape of the step (chosen by the host, see

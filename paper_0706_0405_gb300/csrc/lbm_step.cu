@@ -73,6 +73,7 @@ cudaError_t launch_vec(const float* fin, float* fout, const Model<float>& M, con
 #endif
 constexpr int kTileX = 64, kTileY = LBM_TILE_Y;
 constexpr int kTileThreads = (kTileX / 2) * kTileY;
+
 constexpr int kBoxX = kTileX + 8, kBoxY = kTileY + 2;
 constexpr int kBoxFloats = kBoxX * kBoxY * 9;
 constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages start on 128-byte boundaries
@@ -85,6 +86,22 @@ constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages start on 12
 #ifndef LBM_TILE_MIN_BLOCKS
 #define LBM_TILE_MIN_BLOCKS 6
 #endif
+// How a thread updates its two nodes: together in packed FP32x2 arithmetic
+// (half the arithmetic instructions, one dependency chain) or one after the
+// other in scalar arithmetic (twice the instructions, two chains the
+// scheduler can interleave).  Same bits either way.  Measured on the
+// 4096 x 1024 double Mach reflection: packed is faster for the double-float
+// temperature recovery (69.3 against 67.4 GLUPS) and the plain FP32 mode
+// (78.9 / 77.8), scalar for the FP32 total-energy mode (76.8 / 68.9, where
+// the packed form runs out of registers).  0: scalar in every mode, 1: per
+// mode as measured, 2: packed in every mode.
+#ifndef LBM_TILE_PACKED
+#define LBM_TILE_PACKED 1
+#endif
+template <int TM>
+constexpr bool packed_tile() {
+    return LBM_TILE_PACKED == 2 || (LBM_TILE_PACKED == 1 && (TM == T_DF || TM == T_INT32));
+}
 constexpr int kStages = LBM_TILE_STAGES;
 static_assert(kStages >= 2 && kStages <= 8, "2 to 8 stages");
 constexpr size_t kTileSmem = 128 + sizeof(float) * kStages * kStageFloats + kStages * sizeof(uint64_t);
@@ -154,6 +171,35 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
         const int nvalid = min(2, G.nx - ix0);
         // centre of node ix0 in the box: row ty + 1, column 2 tx + 4 (8-byte aligned)
         const float* b = box + (k % kStages) * kStageFloats + (ty + 1) * R + (2 * tx + 4);
+        const size_t c0 = cell(G, ix0, iy);  // 8-byte aligned: ix0 + PADX is even
+        float* out = fout + c0;
+        if constexpr (packed_tile<TM>()) {
+        // both nodes at once in packed FP32x2 arithmetic (same bits as below)
+        F2 C[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) C[i].v = *reinterpret_cast<const unsigned long long*>(b + i * P);
+        F2 acc[9];
+        {
+            F2 rho, ux, uy, T;
+            moments<float, TM, F2>(C, M, rho, ux, uy, T);
+            bits |= health(lane0(rho), lane0(ux), lane0(uy), lane0(T));
+            if (nvalid == 2) bits |= health(lane1(rho), lane1(ux), lane1(uy), lane1(T));
+            relaxation<float, TM, F2>(M, C, rho, ux, uy, T, acc);
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float* bp = b + i * P;
+            F2 Nn, Ss;
+            Nn.v = *reinterpret_cast<const unsigned long long*>(bp + R);
+            Ss.v = *reinterpret_cast<const unsigned long long*>(bp - R);
+            const F2 Ev = pair(lane1(C[i]), bp[2]), Wv = pair(bp[-1], lane0(C[i]));
+            const F2 o = update<float, F2>(M, i, acc[i], C[i], Ev, Wv, Nn, Ss);
+            if (nvalid == 2)
+                *reinterpret_cast<unsigned long long*>(out + i * pl) = o.v;
+            else
+                out[i * pl] = lane0(o);
+        }
+        } else {
         float2 C[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) C[i] = *reinterpret_cast<const float2*>(b + i * P);
@@ -171,8 +217,6 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
 #pragma unroll
             for (int i = 0; i < 9; ++i) acc[i][j] = ofe[i];
         }
-        const size_t c0 = cell(G, ix0, iy);  // 8-byte aligned: ix0 + PADX is even
-        float* out = fout + c0;
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const float* bp = b + i * P;
@@ -186,6 +230,7 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
                 *reinterpret_cast<float2*>(out + i * pl) = o;
             else
                 out[i * pl] = o.x;
+        }
         }
         // edge nodes also write the next level's ghost cells (values read back)
         const bool edge_row = iy == 0 || iy == G.ny - 1;
@@ -275,13 +320,9 @@ cudaError_t launch_tile_copy(const CUtensorMap& tmap, float* fout, const Grid<fl
     constexpr size_t smem = kTileSmem;
     cudaError_t e = allow_smem<k_tile_copy>(smem);
     if (e != cudaSuccess) return e;
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile_copy, kTileThreads, smem);
     const int tiles_x = (G.nx + kTileX - 1) / kTileX;
     const int ntiles = tiles_x * ((G.ny + kTileY - 1) / kTileY);
-    const int grid = min(ntiles, sms * (per_sm > 0 ? per_sm : 1));
+    const int grid = min(ntiles, full_wave<k_tile_copy>(kTileThreads, smem));
     k_tile_copy<<<grid, kTileThreads, smem, st>>>(tmap, fout, G, status, tiles_x, ntiles);
     return cudaGetLastError();
 }
@@ -301,17 +342,7 @@ cudaError_t launch_tile(const CUtensorMap& tmap, float* fout, const Model<float>
     const int tiles_x = (G.nx + kTileX - 1) / kTileX;
     const int ntiles = tiles_x * ((G.ny + kTileY - 1) / kTileY);
     int grid = grid_hint;
-    if (grid <= 0) {
-        static int full_wave = 0;
-        if (full_wave == 0) {
-            int dev = 0, sms = 0, per_sm = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kTileThreads, smem);
-            full_wave = sms * (per_sm > 0 ? per_sm : 1);
-        }
-        grid = full_wave;
-    }
+    if (grid <= 0) grid = full_wave<k_step_tile<TM>>(kTileThreads, smem);
     if (grid > ntiles) grid = ntiles;
     kern<<<grid, kTileThreads, smem, st>>>(tmap, fout, M, G, level, status, tiles_x, ntiles);
     return cudaGetLastError();
@@ -473,17 +504,7 @@ cudaError_t launch_ring(const float* fin, float* fout, const Model<float>& M, co
         if (e != cudaSuccess) return e;
     }
     int grid = grid_hint;
-    if (grid <= 0) {
-        static int full_wave = 0;  // SMs x resident CTAs per SM, found once per instantiation
-        if (full_wave == 0) {
-            int dev = 0, sms = 0, per_sm = 0;
-            cudaGetDevice(&dev);
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TX, smem);
-            full_wave = sms * (per_sm > 0 ? per_sm : 1);
-        }
-        grid = full_wave;
-    }
+    if (grid <= 0) grid = full_wave<k_step_ring<TX, R, TM>>(TX, smem);
     const int nstrips = (G.nx + TX - 1) / TX;
     const long long total = (long long)nstrips * G.ny;
     const int rows_per_cta = (int)((total + grid - 1) / grid);
