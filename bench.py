@@ -171,32 +171,9 @@ def aggregate(dist, seconds: float, node_updates: float, device=None):
 
 # ------------------------------------------------------------- timing
 
-def timed_steps(lat, steps, stream, every=10):
-    """K single-step launches bracketed by two events, with an event pair
-    around the first launch of every `every` (the other launches of the group
-    go to the library in one call, so host overhead stays off the GPU's
-    critical path); returns (seconds for the K steps, mean duration in ms of
-    the bracketed launches)."""
-    import torch
-    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-             for _ in range((steps + every - 1) // every)]
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    torch.cuda.synchronize()
-    s.record(stream)
-    for g in range(len(pairs)):
-        a, b = pairs[g]
-        a.record(stream)
-        lat.step(1)
-        b.record(stream)
-        rest = min(every, steps - g * every) - 1
-        if rest > 0:
-            lat.step(rest)
-    e.record(stream)
-    e.synchronize()
-    return s.elapsed_time(e) / 1e3, statistics.fmean(a.elapsed_time(b) for a, b in pairs)
-
-
-def plain_steps(lat, steps, stream):
+def timed_steps(lat, steps, stream):
+    """Exactly `steps` steps in one library call between two events on the
+    stream the kernels run on; returns seconds."""
     import torch
     s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
@@ -205,6 +182,23 @@ def plain_steps(lat, steps, stream):
     e.record(stream)
     e.synchronize()
     return s.elapsed_time(e) / 1e3
+
+
+def bracketed_launch_ms(lat, launches, stream):
+    """Diagnostic only (outside every timed region): mean duration of single
+    launches, each between its own pair of events."""
+    import torch
+    pairs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+             for _ in range(launches)]
+    torch.cuda.synchronize()
+    for a, b in pairs:
+        a.record(stream)
+        lat.step(1)
+        b.record(stream)
+    pairs[-1][1].synchronize()
+    return statistics.fmean(a.elapsed_time(b) for a, b in pairs)
+
+
 
 
 # ------------------------------------------------------------- our arm
@@ -229,13 +223,16 @@ def run_ours(args, world, dist):
     if dist:
         dist.barrier()
     with ClockSampler(dev) as clocks:
-        secs, bracketed_ms = timed_steps(lat, args.steps, stream)
+        secs = timed_steps(lat, args.steps, stream)
     # every launch in the timed region is the step kernel (one per step), so
     # the region's event time over the launch count is its mean launch
-    # duration, gaps between launches included; event pairs around single
-    # launches (bracketed_ms) add their own overhead to each measured launch
+    # duration, gaps between launches included
     kernel_ms = secs / args.steps * 1e3
     rate, secs = aggregate(dist, secs, float(p.nodes * args.steps), "cuda")
+    lat.sync()
+    # diagnostic after the timed region: event pairs around single launches
+    # add their own overhead to each measured launch
+    bracketed_ms = bracketed_launch_ms(lat, 10, stream)
     lat.sync()
     launch = lbm.lbm_get_launch(lat.ctx)
     lat.close()
@@ -312,7 +309,8 @@ def extras(args, p, fields, stream):
         n = max(50, args.steps // (40 if prec == "fp64" else 4))
         with lbm.Lattice(p, prec) as lx:
             lx.init(*fields).step(10)
-            secs, bms = timed_steps(lx, n, stream)
+            secs = timed_steps(lx, n, stream)
+            bms = bracketed_launch_ms(lx, 5, stream)
             lx.sync()
         # the same method as the headline: region time over the launches in it
         kms = secs / n * 1e3
@@ -336,10 +334,10 @@ def extras(args, p, fields, stream):
     qf = W.initial_fields(q, seed=0, sigma=0.01)
     with lbm.Lattice(q, args.precision) as la:
         la.init(*qf)
-        fwd_plain = plain_steps(la, q.steps, stream)
+        fwd_plain = timed_steps(la, q.steps, stream)
         la.init(*qf)
         lbm.lbm_record(la.ctx, 50)
-        fwd_rec = plain_steps(la, q.steps, stream)
+        fwd_rec = timed_steps(la, q.steps, stream)
         abar = torch.zeros((9, q.ny, q.nx), dtype=la.dtype, device="cuda")
         lbm.lbm_adjoint_seed(la.ctx, torch.ones((q.ny, q.nx), dtype=la.dtype, device="cuda"), None,
                              None, None, abar)
@@ -350,7 +348,7 @@ def extras(args, p, fields, stream):
     # the plain FP64 forward step on the same tube, for the ratio against it
     with lbm.Lattice(q, "fp64") as l64:
         l64.init(*qf)
-        fwd64 = plain_steps(l64, q.steps, stream)
+        fwd64 = timed_steps(l64, q.steps, stream)
         l64.sync()
     out["adjoint"] = {"workload": q.name, "steps": q.steps, "checkpoint_every": 50,
                       "forward_s": round(fwd_plain, 5), "forward_recording_s": round(fwd_rec, 5),

@@ -290,39 +290,17 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
                     const float* b = box0 + (k & 1) * kStageFloats + (r + !wrap) * kBoxRow + (2 * cx + 4);
                     const int dn = wrap && iy == sG.ny - 1 ? -(sG.ny - 1) * kBoxRow : kBoxRow;
                     const int ds = wrap && iy == 0 ? (sG.ny - 1) * kBoxRow : -kBoxRow;
-                    float2 C[9];
-#pragma unroll
-                    for (int i = 0; i < 9; ++i) C[i] = *reinterpret_cast<const float2*>(b + i * kBoxPop);
-                    float acc[9][2];
-#pragma unroll
-                    for (int j = 0; j < 2; ++j) {
-                        float f[9];
-#pragma unroll
-                        for (int i = 0; i < 9; ++i) f[i] = j ? C[i].y : C[i].x;
-                        float rho, ux, uy, Tt;
-                        moments<float, TM>(f, sM, rho, ux, uy, Tt);
-                        if (j < nvalid) bits |= health(rho, ux, uy, Tt);
-                        float ofe[9];
-                        relaxation<float, TM>(sM, f, rho, ux, uy, Tt, ofe);
-#pragma unroll
-                        for (int i = 0; i < 9; ++i) acc[i][j] = ofe[i];
-                    }
+                    float2 o[9];
+                    bits |= pair_update<TM>(sM, b, kBoxPop, dn, ds, nvalid, o);
                     float* fout = P.f[par ^ 1];
                     const size_t pl = (size_t)sG.plane;
                     float* out = fout + cell(sG, ix0, iy);  // 8-byte aligned: ix0 + PADX is even
 #pragma unroll
                     for (int i = 0; i < 9; ++i) {
-                        const float* bp = b + i * kBoxPop;
-                        const float2 Nn = *reinterpret_cast<const float2*>(bp + dn);
-                        const float2 Ss = *reinterpret_cast<const float2*>(bp + ds);
-                        const float Wv = bp[-1], Ev = bp[2];
-                        float2 o;
-                        o.x = update(sM, i, acc[i][0], C[i].x, C[i].y, Wv, Nn.x, Ss.x);
-                        o.y = update(sM, i, acc[i][1], C[i].y, Ev, C[i].x, Nn.y, Ss.y);
                         if (nvalid == 2)
-                            *reinterpret_cast<float2*>(out + i * pl) = o;
+                            *reinterpret_cast<float2*>(out + i * pl) = o[i];
                         else
-                            out[i * pl] = o.x;
+                            out[i * pl] = o[i].x;
                     }
                     const bool ghost_y = !(wrap && !last);
                     const bool edge_row = ghost_y && (iy == 0 || iy == sG.ny - 1);

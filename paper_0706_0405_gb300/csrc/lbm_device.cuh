@@ -510,6 +510,87 @@ __device__ __forceinline__ void report(unsigned* status, unsigned bits) {
     if (any && (threadIdx.x & 31) == (unsigned)(__ffs(m) - 1)) atomicOr(status, any);
 }
 
+// ---------------------------------------------------- two nodes per thread
+// Update of two x-adjacent nodes from a box in shared memory: b points at the
+// first node's population 0 (8-byte aligned), populations are P floats
+// apart, the rows above and below dn and ds floats away; the x neighbours
+// outside the pair are b[-1] and b[2] of each population.  Writes the nine
+// updated pairs to o and returns the health bits of the nodes inside the
+// grid (nvalid = 1: only the first).
+//
+// Two forms with the same bits: both nodes at once in packed FP32x2
+// arithmetic (half the arithmetic instructions, one dependency chain), or
+// one after the other in scalar arithmetic (twice the instructions, two
+// chains the scheduler can interleave).  Measured on the 4096 x 1024 double
+// Mach reflection: packed is faster for the double-float temperature
+// recovery (69.3 against 67.4 GLUPS) and the plain FP32 mode (78.9 / 77.8),
+// scalar for the FP32 total-energy mode (76.8 / 68.9, where the packed form
+// runs out of registers).  LBM_PAIR_PACKED: 0 scalar in every mode, 1 per
+// mode as measured, 2 packed in every mode.
+#ifndef LBM_PAIR_PACKED
+#define LBM_PAIR_PACKED 1
+#endif
+template <int TM>
+constexpr bool packed_pair() {
+    return LBM_PAIR_PACKED == 2 || (LBM_PAIR_PACKED == 1 && (TM == T_DF || TM == T_INT32));
+}
+
+template <int TM>
+__device__ __forceinline__ unsigned pair_update(const Model<float>& M, const float* b, int P, int dn, int ds,
+                                                int nvalid, float2 (&o)[9]) {
+    unsigned bits = 0;
+    if constexpr (packed_pair<TM>()) {
+        F2 C[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) C[i].v = *reinterpret_cast<const unsigned long long*>(b + i * P);
+        F2 acc[9];
+        {
+            F2 rho, ux, uy, T;
+            moments<float, TM, F2>(C, M, rho, ux, uy, T);
+            bits |= health(lane0(rho), lane0(ux), lane0(uy), lane0(T));
+            if (nvalid == 2) bits |= health(lane1(rho), lane1(ux), lane1(uy), lane1(T));
+            relaxation<float, TM, F2>(M, C, rho, ux, uy, T, acc);
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float* bp = b + i * P;
+            F2 Nn, Ss;
+            Nn.v = *reinterpret_cast<const unsigned long long*>(bp + dn);
+            Ss.v = *reinterpret_cast<const unsigned long long*>(bp + ds);
+            const F2 Ev = pair(lane1(C[i]), bp[2]), Wv = pair(bp[-1], lane0(C[i]));
+            o[i] = lanes(update<float, F2>(M, i, acc[i], C[i], Ev, Wv, Nn, Ss));
+        }
+    } else {
+        float2 C[9];
+#pragma unroll
+        for (int i = 0; i < 9; ++i) C[i] = *reinterpret_cast<const float2*>(b + i * P);
+        float acc[9][2];
+#pragma unroll
+        for (int j = 0; j < 2; ++j) {
+            float f[9];
+#pragma unroll
+            for (int i = 0; i < 9; ++i) f[i] = j ? C[i].y : C[i].x;
+            float rho, ux, uy, T;
+            moments<float, TM>(f, M, rho, ux, uy, T);
+            if (j < nvalid) bits |= health(rho, ux, uy, T);
+            float ofe[9];
+            relaxation<float, TM>(M, f, rho, ux, uy, T, ofe);
+#pragma unroll
+            for (int i = 0; i < 9; ++i) acc[i][j] = ofe[i];
+        }
+#pragma unroll
+        for (int i = 0; i < 9; ++i) {
+            const float* bp = b + i * P;
+            const float2 Nn = *reinterpret_cast<const float2*>(bp + dn);
+            const float2 Ss = *reinterpret_cast<const float2*>(bp + ds);
+            const float Wv = bp[-1], Ev = bp[2];
+            o[i].x = update(M, i, acc[i][0], C[i].x, C[i].y, Wv, Nn.x, Ss.x);
+            o[i].y = update(M, i, acc[i][1], C[i].y, Ev, C[i].x, Nn.y, Ss.y);
+        }
+    }
+    return bits;
+}
+
 // ------------------------------------------------------ one node per thread
 // Reads the node and its four star neighbours of all nine planes (kCoherent:
 // through L2 only, for data written earlier in the same kernel by other

@@ -86,22 +86,6 @@ constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages start on 12
 #ifndef LBM_TILE_MIN_BLOCKS
 #define LBM_TILE_MIN_BLOCKS 6
 #endif
-// How a thread updates its two nodes: together in packed FP32x2 arithmetic
-// (half the arithmetic instructions, one dependency chain) or one after the
-// other in scalar arithmetic (twice the instructions, two chains the
-// scheduler can interleave).  Same bits either way.  Measured on the
-// 4096 x 1024 double Mach reflection: packed is faster for the double-float
-// temperature recovery (69.3 against 67.4 GLUPS) and the plain FP32 mode
-// (78.9 / 77.8), scalar for the FP32 total-energy mode (76.8 / 68.9, where
-// the packed form runs out of registers).  0: scalar in every mode, 1: per
-// mode as measured, 2: packed in every mode.
-#ifndef LBM_TILE_PACKED
-#define LBM_TILE_PACKED 1
-#endif
-template <int TM>
-constexpr bool packed_tile() {
-    return LBM_TILE_PACKED == 2 || (LBM_TILE_PACKED == 1 && (TM == T_DF || TM == T_INT32));
-}
 constexpr int kStages = LBM_TILE_STAGES;
 static_assert(kStages >= 2 && kStages <= 8, "2 to 8 stages");
 constexpr size_t kTileSmem = 128 + sizeof(float) * kStages * kStageFloats + kStages * sizeof(uint64_t);
@@ -173,64 +157,14 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
         const float* b = box + (k % kStages) * kStageFloats + (ty + 1) * R + (2 * tx + 4);
         const size_t c0 = cell(G, ix0, iy);  // 8-byte aligned: ix0 + PADX is even
         float* out = fout + c0;
-        if constexpr (packed_tile<TM>()) {
-        // both nodes at once in packed FP32x2 arithmetic (same bits as below)
-        F2 C[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) C[i].v = *reinterpret_cast<const unsigned long long*>(b + i * P);
-        F2 acc[9];
-        {
-            F2 rho, ux, uy, T;
-            moments<float, TM, F2>(C, M, rho, ux, uy, T);
-            bits |= health(lane0(rho), lane0(ux), lane0(uy), lane0(T));
-            if (nvalid == 2) bits |= health(lane1(rho), lane1(ux), lane1(uy), lane1(T));
-            relaxation<float, TM, F2>(M, C, rho, ux, uy, T, acc);
-        }
+        float2 o[9];
+        bits |= pair_update<TM>(M, b, P, R, -R, nvalid, o);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
-            const float* bp = b + i * P;
-            F2 Nn, Ss;
-            Nn.v = *reinterpret_cast<const unsigned long long*>(bp + R);
-            Ss.v = *reinterpret_cast<const unsigned long long*>(bp - R);
-            const F2 Ev = pair(lane1(C[i]), bp[2]), Wv = pair(bp[-1], lane0(C[i]));
-            const F2 o = update<float, F2>(M, i, acc[i], C[i], Ev, Wv, Nn, Ss);
             if (nvalid == 2)
-                *reinterpret_cast<unsigned long long*>(out + i * pl) = o.v;
+                *reinterpret_cast<float2*>(out + i * pl) = o[i];
             else
-                out[i * pl] = lane0(o);
-        }
-        } else {
-        float2 C[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) C[i] = *reinterpret_cast<const float2*>(b + i * P);
-        float acc[9][2];
-#pragma unroll
-        for (int j = 0; j < 2; ++j) {
-            float f[9];
-#pragma unroll
-            for (int i = 0; i < 9; ++i) f[i] = j ? C[i].y : C[i].x;
-            float rho, ux, uy, T;
-            moments<float, TM>(f, M, rho, ux, uy, T);
-            if (j < nvalid) bits |= health(rho, ux, uy, T);
-            float ofe[9];
-            relaxation<float, TM>(M, f, rho, ux, uy, T, ofe);
-#pragma unroll
-            for (int i = 0; i < 9; ++i) acc[i][j] = ofe[i];
-        }
-#pragma unroll
-        for (int i = 0; i < 9; ++i) {
-            const float* bp = b + i * P;
-            const float2 Nn = *reinterpret_cast<const float2*>(bp + R);
-            const float2 Ss = *reinterpret_cast<const float2*>(bp - R);
-            const float Wv = bp[-1], Ev = bp[2];
-            float2 o;
-            o.x = update(M, i, acc[i][0], C[i].x, C[i].y, Wv, Nn.x, Ss.x);
-            o.y = update(M, i, acc[i][1], C[i].y, Ev, C[i].x, Nn.y, Ss.y);
-            if (nvalid == 2)
-                *reinterpret_cast<float2*>(out + i * pl) = o;
-            else
-                out[i * pl] = o.x;
-        }
+                out[i * pl] = o[i].x;
         }
         // edge nodes also write the next level's ghost cells (values read back)
         const bool edge_row = iy == 0 || iy == G.ny - 1;
