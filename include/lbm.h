@@ -145,17 +145,37 @@ typedef struct lbm_dissipation {
 
 typedef struct lbm_ctx lbm_ctx;
 
+/* Bytes of one level buffer of a context for an nx x ny grid in precision
+ * prec: (ny + 2) x 9 x pitch elements of the storage type, pitch = nx + 8
+ * rounded up to a multiple of 32.  0 for nx, ny outside [1, 2^24] or an
+ * unknown precision.  Needs no GPU. */
+size_t lbm_level_bytes(int nx, int ny, lbm_precision prec);
+
 /* Create a context for an nx x ny grid (nx, ny >= 1).  b > 0, tau > 0,
  * dt > 0, dx > 0; the collision factor per step is dt / tau (Eq. SEC-VON-1
  * with dt equal to the Knudsen number, Sec. 2).  bc[4] in LBM_SIDE_* order.
  * stream: a cudaStream_t (NULL = the legacy default stream) on the current
- * device, which the context keeps using.  Allocates two distribution buffers
- * of (ny + 2) x 9 x pitch elements each (pitch >= nx + 8; internal layout:
- * row-interleaved, each grid row's nine population rows together), owned by the
- * context.  On failure *out is NULL and lbm_last_error(NULL) explains. */
+ * device, which the context keeps using.
+ * The state f of Eq. (SEC-VON-1) lives in two level buffers (the current
+ * level and the next, alternating), each lbm_level_bytes(nx, ny, prec) bytes
+ * in the library's internal layout: row-interleaved, grid row iy + 1 (rows 0
+ * and ny + 1 are ghost rows) holding the nine population rows of that grid
+ * row one after the other, node (ix, iy) at column ix + 4 of each.
+ *  - f_buf0 = f_buf1 = NULL: the context allocates both and frees them in
+ *    lbm_destroy.
+ *  - Both non-NULL: the caller's device memory (e.g. two torch CUDA tensors
+ *    from its own allocator), on the current device, each 256-byte aligned
+ *    and at least lbm_level_bytes long, not overlapping.  The context zeroes
+ *    them here, keeps stepping in them and never frees them; they must stay
+ *    allocated until lbm_destroy returns, and the caller must not write them
+ *    while the context's stream has work queued.  After lbm_destroy they
+ *    still hold the last levels.  Exactly one NULL, a misaligned or
+ *    overlapping pair, or memory that is not device memory of the current
+ *    device gives LBM_E_INVAL.
+ * On failure *out is NULL and lbm_last_error(NULL) explains. */
 lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx,
                       const lbm_dvm* dvm, const lbm_dissipation* diss, const lbm_bc bc[4],
-                      lbm_precision prec, void* stream, lbm_ctx** out);
+                      lbm_precision prec, void* stream, void* f_buf0, void* f_buf1, lbm_ctx** out);
 
 /* Free everything the context owns (waits for its stream first). NULL is a
  * no-op. */
@@ -279,7 +299,9 @@ lbm_status lbm_get_launch(const lbm_ctx* ctx, lbm_launch* launch);
 lbm_status lbm_autotune(lbm_ctx* ctx, int steps, lbm_launch* best, double* ms, int* n_candidates);
 
 /* FP64 conservation totals (out[0..3] = sum rho, sum rho ux, sum rho uy,
- * sum rho (b T + u^2), as lbm_conservation) of a dense 9 x ny x nx
+ * sum rho (b T + u^2), the quantities of lbm_conservation; the two sum in
+ * different orders, so they agree to rounding, about 1e-15 relative, not
+ * bit for bit) of a dense 9 x ny x nx
  * distribution f in device memory (the layout lbm_get_f writes; element type
  * double for LBM_FP64, float for the FP32 modes), for callers that cannot
  * allocate device memory: a process whose device memory is committed to a
@@ -291,9 +313,12 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps, lbm_launch* best, double* ms, i
  *    every GPU that loads the library until the process exits.  It bounds
  *    nx * ny to 8 388 608 nodes (2048 tiles of 4096); larger grids get
  *    LBM_E_INVAL.
- *  - The first call on each device looks up that array's device address (a
- *    one-time set-up, with the device current); make that first call before
- *    any stream capture.
+ *  - The first call in each CUDA context (normally once per device, in the
+ *    runtime's primary context) looks up that array's device address in
+ *    that context, with the device current, and keeps it under the
+ *    context's unique ID; a non-primary context, or a new primary context
+ *    after cudaDeviceReset, does its own look-up.  Make that first call
+ *    before any stream capture.
  *  - All calls share the array; calls that overlap on the GPU race and may
  *    return wrong totals.  Each call writes every value it reads, so a call
  *    never depends on an earlier call's contents.

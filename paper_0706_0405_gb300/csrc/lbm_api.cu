@@ -445,13 +445,30 @@ const char* lbm_last_error(const lbm_ctx* ctx) {
     return ctx ? ctx->err.c_str() : g_create_err.c_str();
 }
 
+size_t lbm_level_bytes(int nx, int ny, lbm_precision prec) {
+    if (nx < 1 || ny < 1 || nx > (1 << 24) || ny > (1 << 24) || prec < LBM_FP64 || prec > LBM_FP32_CONS) return 0;
+    const size_t pitch = (size_t)((nx + 2 * PADX) + 31) / 32 * 32;
+    return (size_t)(ny + 2) * 9 * pitch * (prec == LBM_FP64 ? 8 : 4);
+}
+
 lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx, const lbm_dvm* dvm,
                       const lbm_dissipation* diss, const lbm_bc bc[4], lbm_precision prec,
-                      void* stream, lbm_ctx** out) {
+                      void* stream, void* f_buf0, void* f_buf1, lbm_ctx** out) {
     if (!out) return fail(nullptr, LBM_E_INVAL, "out must not be NULL");
     *out = nullptr;
     lbm_status s = validate(nx, ny, b, tau, dt, dx, dvm, diss, bc, prec);
     if (s != LBM_OK) return s;
+    const bool caller_f = f_buf0 || f_buf1;
+    if (caller_f) {
+        if (!f_buf0 || !f_buf1)
+            return fail(nullptr, LBM_E_INVAL, "f_buf0 and f_buf1 must both be given or both be NULL");
+        const size_t need = lbm_level_bytes(nx, ny, prec);
+        const uintptr_t a0 = reinterpret_cast<uintptr_t>(f_buf0), a1 = reinterpret_cast<uintptr_t>(f_buf1);
+        if ((a0 | a1) % 256 != 0)
+            return fail(nullptr, LBM_E_INVAL, "f_buf0 and f_buf1 must be 256-byte aligned");
+        if ((a0 < a1 ? a1 - a0 : a0 - a1) < need)
+            return fail(nullptr, LBM_E_INVAL, "f_buf0 and f_buf1 overlap (each needs %zu bytes)", need);
+    }
     lbm_ctx* c = new lbm_ctx();
     if (cudaGetDevice(&c->device) != cudaSuccess) {
         cudaGetLastError();
@@ -480,7 +497,25 @@ lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx
     c->gf = build_grid<float>(*c, c->md);
     const size_t fbytes = level_bytes(c);
     cudaError_t e = cudaSuccess;
-    for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = dev_malloc(&c->f[k], fbytes);
+    if (caller_f) {
+        // the caller's buffers: device memory of this context's device
+        void* bufs[2] = {f_buf0, f_buf1};
+        for (int k = 0; k < 2; ++k) {
+            cudaPointerAttributes at{};
+            const bool dev_ok = cudaPointerGetAttributes(&at, bufs[k]) == cudaSuccess &&
+                                (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) &&
+                                at.device == c->device;
+            cudaGetLastError();
+            if (!dev_ok) {
+                delete c;
+                return fail(nullptr, LBM_E_INVAL, "f_buf%d is not device memory of the current device", k);
+            }
+            c->f[k] = bufs[k];
+        }
+        c->f_owned = false;
+    } else {
+        for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = dev_malloc(&c->f[k], fbytes);
+    }
     if (e == cudaSuccess) e = dev_malloc((void**)&c->d_status, sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_status, sizeof(unsigned));
     const int np = c->prec == LBM_FP64 ? conservation_partials(c->gd) : conservation_partials(c->gf);
@@ -506,8 +541,10 @@ void lbm_destroy(lbm_ctx* c) {
     if (!c) return;
     cudaSetDevice(c->device);
     cudaStreamSynchronize(c->stream);
-    cudaFree(c->f[0]);
-    cudaFree(c->f[1]);
+    if (c->f_owned) {  // caller-owned level buffers are never freed here
+        cudaFree(c->f[0]);
+        cudaFree(c->f[1]);
+    }
     cudaFree(c->d_status);
     cudaFreeHost(c->h_status);
     cudaFree(c->d_partials);

@@ -152,7 +152,8 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
     for (int p = 0; p < nprob; ++p) {
         const lbm_problem& q = probs[p];
         lbm_ctx* c = nullptr;
-        lbm_status s = lbm_create(q.nx, q.ny, q.b, q.tau, q.dt, q.dx, &q.dvm, &q.diss, q.bc, prec, stream, &c);
+        lbm_status s = lbm_create(q.nx, q.ny, q.b, q.tau, q.dt, q.dx, &q.dvm, &q.diss, q.bc, prec, stream, nullptr,
+                                  nullptr, &c);
         if (s != LBM_OK) {
             std::string m = "problem " + std::to_string(p) + ": " + g_create_err;
             lbm_batch_destroy(b);

@@ -33,6 +33,7 @@ struct lbm_ctx {
     lbm_bc bc[4]{};
     cudaStream_t stream = nullptr;
     void* f[2] = {nullptr, nullptr};
+    bool f_owned = true;    // false: f[0], f[1] belong to the caller (lbm_create's f_buf0, f_buf1)
     int cur = 0;            // buffer holding the current level
     long long step = 0;     // step index of the current level
     bool ready = false;     // lbm_init / lbm_set_f / lbm_load done

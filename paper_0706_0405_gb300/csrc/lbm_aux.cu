@@ -1,6 +1,7 @@
 // lbm_aux.cu -- initialisation, ghost fill, moments output, FP64 conservation
 // totals and interior pack/unpack kernels of liblbm.
 #include "lbm_launch.h"
+#include "lbm_reduce.cuh"
 
 namespace lbm {
 
@@ -114,20 +115,6 @@ int conservation_partials(const Grid<S>& G) {
     return (int)(nb < kConsBlocks ? (nb < 1 ? 1 : nb) : kConsBlocks);
 }
 
-__device__ __forceinline__ void block_sum4(double (&v)[4], double (*sh)[kThreads]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = v[q];
-    __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
-        __syncthreads();
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = sh[q][0];
-}
-
 template <typename S>
 __global__ void __launch_bounds__(kThreads) k_cons_partial(const S* __restrict__ f,
                                                            const Model<double> M,
@@ -150,7 +137,7 @@ __global__ void __launch_bounds__(kThreads) k_cons_partial(const S* __restrict__
         acc[2] += M.c1 * (v[4] - v[2]) + M.d * ((v[7] + v[8]) - (v[5] + v[6]));
         acc[3] += M.eta2 * v[0] + M.c1s * s14 + M.c2s * s58;
     }
-    block_sum4(acc, sh);
+    block_sum4<kThreads>(acc, sh);
     if (threadIdx.x == 0)
 #pragma unroll
         for (int q = 0; q < 4; ++q) partials[q * gridDim.x + blockIdx.x] = acc[q];
@@ -163,7 +150,7 @@ __global__ void __launch_bounds__(kThreads) k_cons_final(const double* __restric
     for (int b = threadIdx.x; b < nparts; b += kThreads)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] += partials[q * nparts + b];
-    block_sum4(acc, sh);
+    block_sum4<kThreads>(acc, sh);
     if (threadIdx.x == 0)
 #pragma unroll
         for (int q = 0; q < 4; ++q) out[q] = acc[q];

@@ -21,10 +21,13 @@
 // wrong totals: order them.
 #include <cmath>
 #include <mutex>
+#include <vector>
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include "../../include/lbm.h"
+#include "lbm_reduce.cuh"
 
 namespace {
 
@@ -37,25 +40,62 @@ constexpr int kScratchDoubles = 4 * kMaxTiles + 4;                  // partials 
 
 __device__ __align__(256) double g_scratch[kScratchDoubles];
 
-// Host copies of &g_scratch per device (the symbol's name is only a host-side
-// stand-in; the device address is obtained once per device with that device
-// current).
-constexpr int kMaxDevices = 64;
-double* g_scratch_dev[kMaxDevices] = {nullptr};
+// Device addresses of g_scratch, one per CUDA context that has called in.
+// The symbol's name is only a host-side stand-in: its device address belongs
+// to the module as loaded in one context, so it is looked up (with that
+// context current) the first time a context calls, and kept under the
+// context's unique ID, which the driver never hands out twice.  A caller on a
+// non-primary context, or on a new primary context after cudaDeviceReset,
+// therefore gets an address of its own context.  Without the driver's
+// context queries the address is looked up on every call.
+struct ScratchAddr {
+    unsigned long long ctx_id;
+    double* ptr;
+};
+std::vector<ScratchAddr> g_scratch_addrs;
 std::mutex g_setup_mutex;
 
-__device__ __forceinline__ void block_sum4(double (&v)[4], double (*sh)[kThreads]) {
-#pragma unroll
-    for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] = v[q];
-    __syncthreads();
-    for (int s = kThreads / 2; s > 0; s >>= 1) {
-        if ((int)threadIdx.x < s)
-#pragma unroll
-            for (int q = 0; q < 4; ++q) sh[q][threadIdx.x] += sh[q][threadIdx.x + s];
-        __syncthreads();
+typedef CUresult (*CtxGetCurrentFn)(CUcontext*);
+typedef CUresult (*CtxGetIdFn)(CUcontext, unsigned long long*);
+
+template <typename Fn>
+Fn driver_fn(const char* name, int version) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion(name, &p, version, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+        cudaGetLastError();
+        return nullptr;
     }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) v[q] = sh[q][0];
+    return reinterpret_cast<Fn>(p);
+}
+
+// The current context's unique ID, or 0 if it cannot be had.
+unsigned long long current_context_id() {
+    static const CtxGetCurrentFn get_current = driver_fn<CtxGetCurrentFn>("cuCtxGetCurrent", 4000);
+    static const CtxGetIdFn get_id = driver_fn<CtxGetIdFn>("cuCtxGetId", 12000);
+    CUcontext ctx = nullptr;
+    unsigned long long id = 0;
+    if (!get_current || !get_id || get_current(&ctx) != CUDA_SUCCESS || !ctx || get_id(ctx, &id) != CUDA_SUCCESS)
+        return 0;
+    return id;
+}
+
+// &g_scratch in the current context (nullptr on failure).  Call with the
+// caller's device current and the runtime initialised on it.
+double* scratch_address() {
+    const unsigned long long id = current_context_id();
+    std::lock_guard<std::mutex> lock(g_setup_mutex);
+    if (id != 0)
+        for (const ScratchAddr& a : g_scratch_addrs)
+            if (a.ctx_id == id) return a.ptr;
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    if (id != 0) g_scratch_addrs.push_back({id, static_cast<double*>(p)});
+    return static_cast<double*>(p);
 }
 
 // Partial totals of one tile of kTile nodes of a dense 9 x n distribution
@@ -81,7 +121,7 @@ __global__ void __launch_bounds__(kThreads)
         acc[2] += c1 * (v[4] - v[2]) + d * ((v[7] + v[8]) - (v[5] + v[6]));
         acc[3] += eta2 * v[0] + c1s * s14 + c2s * s58;
     }
-    block_sum4(acc, sh);
+    lbm::block_sum4<kThreads>(acc, sh);
     if (threadIdx.x == 0)
 #pragma unroll
         for (int q = 0; q < 4; ++q) scratch[q * gridDim.x + blockIdx.x] = acc[q];
@@ -95,7 +135,7 @@ __global__ void __launch_bounds__(kThreads) k_totals_final(double* __restrict__ 
     for (int b = threadIdx.x; b < ntiles; b += kThreads)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] += scratch[q * ntiles + b];
-    block_sum4(acc, sh);
+    lbm::block_sum4<kThreads>(acc, sh);
     if (threadIdx.x == 0)
 #pragma unroll
         for (int q = 0; q < 4; ++q) scratch[4 * kMaxTiles + q] = acc[q];
@@ -111,23 +151,12 @@ extern "C" lbm_status lbm_conservation_noalloc(const void* f, int nx, int ny, lb
     if (n > kMaxNodes) return LBM_E_INVAL;  // more tiles than the static scratch holds
     if (prec < LBM_FP64 || prec > LBM_FP32_CONS) return LBM_E_INVAL;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
         cudaGetLastError();
         return LBM_E_CUDA;
     }
-    double* scratch = nullptr;
-    {
-        std::lock_guard<std::mutex> lock(g_setup_mutex);
-        if (g_scratch_dev[dev] == nullptr) {
-            void* p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) {
-                cudaGetLastError();
-                return LBM_E_CUDA;
-            }
-            g_scratch_dev[dev] = static_cast<double*>(p);
-        }
-        scratch = g_scratch_dev[dev];
-    }
+    double* scratch = scratch_address();
+    if (!scratch) return LBM_E_CUDA;
     const cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int ntiles = (int)((n + kTile - 1) / kTile);
     const double d = dvm->c2 / std::sqrt(2.0);

@@ -33,7 +33,7 @@ EXPORTS = ("lbm_create", "lbm_destroy", "lbm_last_error", "lbm_init", "lbm_step"
            "lbm_batch_step", "lbm_batch_sync", "lbm_batch_problem", "lbm_batch_info",
            "lbm_probe_rates", "lbm_vn_scan", "lbm_batch_set_launch", "lbm_batch_get_launch",
            "lbm_batch_autotune", "lbm_probe_tile_copy", "lbm_batch_set_wait_limit", "lbm_batch_plant_stall",
-           "lbm_inject_alloc_failure")
+           "lbm_inject_alloc_failure", "lbm_level_bytes")
 LBM_FLAG_NONPHYSICAL, LBM_FLAG_TIMEOUT, LBM_FLAG_T_NONPOSITIVE = 1, 2, 4
 
 
@@ -103,7 +103,8 @@ def load():
     sig = {
         "lbm_create": ([ctypes.c_int, ctypes.c_int] + [ctypes.c_double] * 4 +
                        [ctypes.POINTER(lbm_dvm), ctypes.POINTER(lbm_dissipation),
-                        ctypes.POINTER(lbm_bc), ctypes.c_int, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+                        ctypes.POINTER(lbm_bc), ctypes.c_int, _VP, _VP, _VP, ctypes.POINTER(_VP)], ctypes.c_int),
+        "lbm_level_bytes": ([ctypes.c_int, ctypes.c_int, ctypes.c_int], ctypes.c_size_t),
         "lbm_destroy": ([ctx], None),
         "lbm_last_error": ([ctx], ctypes.c_char_p),
         "lbm_init": ([ctx, _VP, _VP, _VP, _VP], ctypes.c_int),
@@ -191,15 +192,24 @@ def lbm_version() -> str:
     return load().lbm_version().decode()
 
 
-def lbm_create(nx, ny, b, tau, dt, dx, dvm, diss, bc, prec, stream=None):
-    """Returns the context handle (int).  ``bc`` is a sequence of 4 lbm_bc."""
+def _prec(prec) -> int:
+    return PRECISIONS.get(prec, prec) if isinstance(prec, str) else int(prec)
+
+
+def lbm_level_bytes(nx, ny, prec) -> int:
+    """Bytes of one level buffer of a context (0 for invalid arguments)."""
+    return int(load().lbm_level_bytes(int(nx), int(ny), _prec(prec)))
+
+
+def lbm_create(nx, ny, b, tau, dt, dx, dvm, diss, bc, prec, stream=None, f_buf0=None, f_buf1=None):
+    """Returns the context handle (int).  ``bc`` is a sequence of 4 lbm_bc;
+    f_buf0 / f_buf1: optional caller-owned level buffers (device memory)."""
     lib = load()
     arr = (lbm_bc * 4)(*bc)
     out = _VP()
     st = lib.lbm_create(int(nx), int(ny), float(b), float(tau), float(dt), float(dx),
-                        ctypes.byref(dvm), ctypes.byref(diss), arr,
-                        PRECISIONS.get(prec, prec) if isinstance(prec, str) else int(prec),
-                        _ptr(stream), ctypes.byref(out))
+                        ctypes.byref(dvm), ctypes.byref(diss), arr, _prec(prec),
+                        _ptr(stream), _ptr(f_buf0), _ptr(f_buf1), ctypes.byref(out))
     _check(None, st)
     return out.value
 
@@ -569,10 +579,18 @@ class Batch:
 class Lattice:
     """One liblbm context for a problem (attributes of workloads.Problem).
 
-    ``stream`` defaults to torch's current CUDA stream.  Results come back as
-    torch CUDA tensors of the storage dtype (or numpy when asked)."""
+    ``stream`` defaults to torch's current CUDA stream.  ``buffers``: optional
+    pair of caller-owned CUDA tensors (or device addresses) that hold the two
+    levels of f, each at least ``Lattice.level_bytes(p, precision)`` bytes
+    and 256-byte aligned; the Lattice keeps them referenced while it lives
+    and never frees them.  Results come back as torch CUDA tensors of the
+    storage dtype."""
 
-    def __init__(self, p, precision: str = "fp64", stream=None):
+    @staticmethod
+    def level_bytes(p, precision: str) -> int:
+        return lbm_level_bytes(p.nx, p.ny, precision)
+
+    def __init__(self, p, precision: str = "fp64", stream=None, buffers=None):
         import torch
         self.p = p
         self.precision = precision
@@ -586,8 +604,9 @@ class Lattice:
         diss.beta = float(p.beta)
         for i in range(9):
             diss.lambda_[i] = float(p.lam[i])
+        self.buffers = tuple(buffers) if buffers is not None else (None, None)
         self.ctx = lbm_create(p.nx, p.ny, p.b, p.tau, p.dt, p.dx, dvm, diss,
-                              [make_bc(s) for s in p.sides], precision, stream)
+                              [make_bc(s) for s in p.sides], precision, stream, *self.buffers)
 
     def close(self):
         if self.ctx:

@@ -73,6 +73,29 @@ def test_create_rejects_invalid_arguments(over, msg):
     assert msg in str(ei.value)
 
 
+def test_level_bytes_is_the_padded_row_interleaved_level():
+    # (ny + 2) rows x 9 populations x pitch, pitch = nx + 8 rounded up to 32
+    assert lbm.lbm_level_bytes(400, 4, "fp64") == 6 * 9 * 416 * 8
+    assert lbm.lbm_level_bytes(400, 4, "fp32_tdf") == 6 * 9 * 416 * 4
+    assert lbm.lbm_level_bytes(4096, 1024, "fp32") == 1026 * 9 * 4128 * 4
+    assert lbm.lbm_level_bytes(1, 1, "fp32") == 3 * 9 * 32 * 4
+    for bad in ((0, 4, "fp64"), (4, -1, "fp64"), (1 << 25, 4, "fp32"), (4, 4, 9)):
+        assert lbm.lbm_level_bytes(*bad) == 0
+
+
+@pytest.mark.parametrize("bufs,msg", [
+    ((1 << 20, None), "both"), ((None, 1 << 20), "both"),
+    (((1 << 20) + 16, 1 << 24), "aligned"), ((1 << 20, (1 << 20) + 256), "overlap"),
+])
+def test_create_rejects_bad_caller_buffers_before_touching_them(bufs, msg):
+    # rejected by the argument checks alone: the addresses are never used
+    p = W.sod_400x4()
+    with pytest.raises(lbm.LbmError) as ei:
+        lbm.lbm_create(*_args(p), None, *bufs)
+    assert ei.value.status == lbm.LBM_E_INVAL
+    assert msg in str(ei.value)
+
+
 def test_calls_on_null_context_fail_cleanly():
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_step(None, 1)

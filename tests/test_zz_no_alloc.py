@@ -17,8 +17,11 @@ def test_noalloc_rejects_sizes_beyond_its_scratch():
     with pytest.raises(lbm.LbmError) as ei:
         lbm.lbm_conservation_noalloc(1, 4096, 2049, "fp32", dvm)  # 8 392 704 > 8 388 608 nodes
     assert ei.value.status == lbm.LBM_E_INVAL
-    with pytest.raises(lbm.LbmError):
-        lbm.lbm_conservation_noalloc(1, 0, 5, "fp32", dvm)
+    # checked before any CUDA call: each gives LBM_E_INVAL, not LBM_E_CUDA
+    for args in ((1, 0, 5, "fp32"), (1, 5, 0, "fp32"), (1, 5, 5, 9), (None, 5, 5, "fp32")):
+        with pytest.raises(lbm.LbmError) as ei:
+            lbm.lbm_conservation_noalloc(*args, dvm)
+        assert ei.value.status == lbm.LBM_E_INVAL, args
 
 
 @pytest.mark.gpu
