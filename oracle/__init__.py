@@ -84,6 +84,8 @@ def _load():
         lib.kt_init.argtypes = [cfgp, _D, _D, _D, _D, _D]
         lib.kt_run.argtypes = [cfgp, _D, _D, ctypes.c_long, ctypes.c_long]
         lib.kt_run.restype = ctypes.c_long
+        lib.kt_run_f32_storage.argtypes = [cfgp, _D, _D, ctypes.c_long, ctypes.c_long]
+        lib.kt_run_f32_storage.restype = ctypes.c_long
         lib.kt_step_nodes.argtypes = [cfgp, _D, ctypes.c_long, _L, ctypes.c_long, _D]
         lib.kt_fields.argtypes = [cfgp, _D, _D, _D, _D, _D]
         lib.kt_sums.argtypes = [cfgp, _D, _D]
@@ -174,12 +176,16 @@ def fill_ghosts(p, f: np.ndarray, t: float) -> None:
     _load().kt_fill_ghosts(ctypes.byref(c), _ptr(f), float(t))
 
 
-def run(p, f: np.ndarray, nsteps: int, n0: int = 0) -> int:
+def run(p, f: np.ndarray, nsteps: int, n0: int = 0, f32_storage: bool = False) -> int:
     """Advance f in place by nsteps steps from step index n0; returns the
-    number of nodes left with rho <= 0, T <= 0 or a non-finite velocity."""
+    number of nodes left with rho <= 0, T <= 0 or a non-finite velocity.
+    f32_storage: keep the state rounded to FP32 between steps (FP64
+    arithmetic), the error floor of any FP32-storage implementation; this
+    rounds f itself first."""
     c = config(p)
     work = np.empty_like(f)
-    return int(_load().kt_run(ctypes.byref(c), _ptr(f), _ptr(work), int(nsteps), int(n0)))
+    fn = _load().kt_run_f32_storage if f32_storage else _load().kt_run
+    return int(fn(ctypes.byref(c), _ptr(f), _ptr(work), int(nsteps), int(n0)))
 
 
 def step_nodes(p, f: np.ndarray, n: int, nodes) -> np.ndarray:

@@ -313,6 +313,50 @@ long kt_run(const kt_config* c, double* f, double* work, long nsteps, long n0) {
     return bad;
 }
 
+/* The same steps with the state held in FP32 between steps, the arithmetic
+ * still FP64: after each ghost fill and each update, every stored value is
+ * rounded to the nearest FP32 number.  Not from the paper: this is the floor
+ * that an FP32 state (the storage of the library's FP32 modes) puts under
+ * the error of any implementation that stores f in FP32, whatever precision
+ * its arithmetic has. */
+static void round_to_f32(double* v, size_t len) {
+    for (size_t q = 0; q < len; ++q) v[q] = (double)(float)v[q];
+}
+
+long kt_run_f32_storage(const kt_config* c, double* f, double* work, long nsteps, long n0) {
+    const size_t len = kt_field_len(c);
+    double* a = f;
+    double* bnew = work;
+    round_to_f32(a, len);
+    for (long s = 0; s < nsteps; ++s) {
+        double t = (double)(n0 + s) * c->dt;
+        kt_fill_ghosts(c, a, t);
+        round_to_f32(a, len);
+#ifdef _OPENMP
+#pragma omp parallel for collapse(2) schedule(static) num_threads(omp_threads)
+#endif
+        for (int k = 1; k <= c->ny; ++k) {
+            for (int j = 1; j <= c->nx; ++j) {
+                double out[9];
+                node_update(c, a, k, j, out);
+                for (int i = 0; i < 9; ++i) bnew[at(c, i, k, j)] = (double)(float)out[i];
+            }
+        }
+        double* tmp = a;
+        a = bnew;
+        bnew = tmp;
+    }
+    if (a != f) memcpy(f, a, len * sizeof(double));
+    long bad = 0;
+    for (int k = 1; k <= c->ny; ++k)
+        for (int j = 1; j <= c->nx; ++j) {
+            double v[9];
+            for (int i = 0; i < 9; ++i) v[i] = f[at(c, i, k, j)];
+            bad += nonphysical(c, v);
+        }
+    return bad;
+}
+
 /* One step evaluated only at the listed interior nodes (node = kk * nx + jj),
  * from the level-n state f at step index n.  f's ghost layer is (re)filled
  * for time n dt.  out receives count x 9 values. */

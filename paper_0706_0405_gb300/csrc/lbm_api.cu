@@ -92,7 +92,9 @@ Model<double> build_model(double b, double tau, double dt, double dx, const lbm_
         const double mag = i == 0 ? 0.0 : (i <= 4 ? c1 : M.d);
         const double ax = SGX[i] * mag * r, ay = SGY[i] * mag * r;
         const double mu = diss.lambda[i] * dt / (dx * dx);
-        double C = 1.0 - M.omega - 4.0 * mu, E = mu, Wt = mu, N = mu, Sd = mu;
+        // C: the stencil's own centre weight; w[i][0] adds the identity and
+        // the -omega of the relaxation
+        double C = -4.0 * mu, E = mu, Wt = mu, N = mu, Sd = mu;
         if (SGX[i] >= 0) {  // Eq. (SEC-VON-2a)
             E -= ax * beta;
             C -= ax * (1.0 - 2.0 * beta);
@@ -111,7 +113,8 @@ Model<double> build_model(double b, double tau, double dt, double dx, const lbm_
             C += ay * (1.0 - 2.0 * beta);
             Sd += ay * beta;
         }
-        M.w[i][0] = C;
+        M.w[i][0] = (1.0 - M.omega) + C;
+        M.wi[i] = C;
         M.w[i][1] = E;
         M.w[i][2] = Wt;
         M.w[i][3] = N;

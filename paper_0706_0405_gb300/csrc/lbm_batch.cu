@@ -291,7 +291,7 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
                     const int dn = wrap && iy == sG.ny - 1 ? -(sG.ny - 1) * kBoxRow : kBoxRow;
                     const int ds = wrap && iy == 0 ? (sG.ny - 1) * kBoxRow : -kBoxRow;
                     float2 o[9];
-                    bits |= pair_update<TM>(sM, b, kBoxPop, dn, ds, nvalid, o);
+                    bits |= pair_update<TM, false>(sM, b, kBoxPop, dn, ds, nvalid, o);
                     float* fout = P.f[par ^ 1];
                     const size_t pl = (size_t)sG.plane;
                     float* out = fout + cell(sG, ix0, iy);  // 8-byte aligned: ix0 + PADX is even

@@ -47,10 +47,14 @@ enum Side : int { S_LEFT = 0, S_RIGHT = 1, S_BOTTOM = 2, S_TOP = 3 };
 // derivative of Eqs. SEC-VON-2a/2b and central second differences folded in):
 //   f_i' = w[i][0] f_i(x) + w[i][1] f_i(x+dx) + w[i][2] f_i(x-dx)
 //        + w[i][3] f_i(y+dy) + w[i][4] f_i(y-dy) + omega f_i^eq(x),
-// where w[i][0] already holds the -omega of the relaxation.
+// where w[i][0] already holds the 1 - omega of the identity and the
+// relaxation; wi[i] = w[i][0] - (1 - omega) is the stencil's own centre
+// weight, for the increment form f_i' = f_i + (stencil + relaxation
+// increment) of the FP32 modes.
 template <typename S>
 struct Model {
     S w[9][5];
+    S wi[9];
     S omega;          // dt / tau
     S c1, d;          // axis speed c1; diagonal component c2 / sqrt(2)
     S c1s, c2s, eta2; // c1^2, c2^2, eta0^2
@@ -343,32 +347,29 @@ __device__ __forceinline__ void omega_equilibrium(const Model<S>& M, V rho, V ux
     equilibrium_scaled<S, V>(M, mul_(M.omega, rho), ux, uy, T, ofe);
 }
 
-// Moment-exact relaxation term.  In FP32 the equilibrium evaluated from
-// FP32 moments does not carry exactly the mass, momentum and energy it was
-// built from: at high Mach the internal energy is a small part of terms of
-// size u^2, so each evaluation shifts T by a fixed relative amount of order
-// 2^-24 u^2 / T, and the same shift recurs every step in a uniform stream
-// (a drift that reaches tens of per cent over 10^4-10^5 steps at Mach 30).
-// The defects d_i = omega f^eq_i - omega f_i are formed one population at a
-// time (one rounding each, so they are accurate even where they are tiny)
-// and their moments are removed with the fewest populations:
+// Moment-exact relaxation.  In FP32 the equilibrium evaluated from FP32
+// moments does not carry exactly the mass, momentum and energy it was built
+// from: at high Mach the internal energy is a small part of terms of size
+// u^2, so each evaluation shifts T by a fixed relative amount of order
+// 2^-24 u^2 / T, and the same shift recurs every step in a uniform stream (a
+// drift that reaches tens of per cent over 10^4-10^5 steps at Mach 30).  The
+// relaxation increments d_i = omega f^eq_i - omega f_i are formed one
+// population at a time (one rounding each, so they are accurate even where
+// they are tiny) and their moments are removed with the fewest populations:
 //  * momentum by the opposite axis pairs (3, 1) and (4, 2):
-//    f3 -= g_x, f1 += g_x with g_x = d j_x / (2 c1) (mass and |v|^2 unchanged);
+//    d3 -= g_x, d1 += g_x with g_x = (momentum of d)_x / (2 c1) (mass and
+//    |v|^2 unchanged);
 //  * mass and energy by the rest population and one set of four moving
-//    populations s (axes or diagonals, speed c_s, sum of v = 0): adding
-//    delta_0 and delta_s to each of the set keeps the momentum and removes
-//    mass sum d and energy sum d (|v|^2 + eta^2) when
-//    delta_s = -(S_s + rho_o S_o) / 4 and delta_0 = -d_0 - (1 - rho_o) S_o,
-//    S_s, S_o the defect sums of the set and of the other set.
-// Then omega f^eq has exactly (up to the final roundings) omega times the
-// mass, momentum and energy of f (Eqs. e4, e5, e7), as it has in exact
-// arithmetic, and the collision conserves them.
+//    populations s (axes or diagonals, speed c_s, sum of v = 0): with S_s,
+//    S_o the increment sums of the set and of the other set,
+//    d_j += -(S_s + rho_o S_o) / 4 for the set and d_0 = -(1 - rho_o) S_o,
+//    which removes mass sum d and energy sum d (|v|^2 + eta^2).
+// Then d carries no mass, momentum or energy (up to its own final roundings,
+// relative to the small increments), as in exact arithmetic, and the
+// collision conserves them (Eqs. e4, e5, e7).
 template <typename S, int TM, typename V = S>
-__device__ __forceinline__ void conserve(const Model<S>& M, const V (&f)[9], V (&ofe)[9]) {
+__device__ __forceinline__ void conserve_increment(const Model<S>& M, V (&d)[9]) {
     if constexpr (moment_exact<TM>()) {
-        V d[9];
-#pragma unroll
-        for (int i = 0; i < 9; ++i) d[i] = fma_(-M.omega, f[i], ofe[i]);
         const V sa = add_(add_(d[1], d[3]), add_(d[2], d[4]));
         const V sd = add_(add_(d[5], d[7]), add_(d[6], d[8]));
         const V djx = fma_(M.c1, sub_(d[3], d[1]), mul_(M.d, sub_(add_(d[6], d[7]), add_(d[5], d[8]))));
@@ -376,42 +377,61 @@ __device__ __forceinline__ void conserve(const Model<S>& M, const V (&f)[9], V (
         const V gx = mul_(djx, M.h1), gy = mul_(djy, M.h1);
         if (M.cons_diag == S(0)) {
             const V t = fma_(sd, M.kcons, mul_(sa, S(0.25)));  // -delta_s
-            ofe[0] = sub_(ofe[0], fma_(sd, M.kzero, d[0]));
-            ofe[1] = sub_(add_(ofe[1], gx), t);
-            ofe[3] = sub_(sub_(ofe[3], gx), t);
-            ofe[2] = sub_(add_(ofe[2], gy), t);
-            ofe[4] = sub_(sub_(ofe[4], gy), t);
+            d[0] = mul_(sd, -M.kzero);
+            d[1] = sub_(add_(d[1], gx), t);
+            d[3] = sub_(sub_(d[3], gx), t);
+            d[2] = sub_(add_(d[2], gy), t);
+            d[4] = sub_(sub_(d[4], gy), t);
         } else {
             const V t = fma_(sa, M.kcons, mul_(sd, S(0.25)));
-            ofe[0] = sub_(ofe[0], fma_(sa, M.kzero, d[0]));
-            ofe[1] = add_(ofe[1], gx);
-            ofe[3] = sub_(ofe[3], gx);
-            ofe[2] = add_(ofe[2], gy);
-            ofe[4] = sub_(ofe[4], gy);
+            d[0] = mul_(sa, -M.kzero);
+            d[1] = add_(d[1], gx);
+            d[3] = sub_(d[3], gx);
+            d[2] = add_(d[2], gy);
+            d[4] = sub_(d[4], gy);
 #pragma unroll
-            for (int i = 5; i < 9; ++i) ofe[i] = sub_(ofe[i], t);
+            for (int i = 5; i < 9; ++i) d[i] = sub_(d[i], t);
         }
     }
 }
 
-// omega f^eq of the node's own moments, moment-exact in the modes that ask
-// for it: the relaxation term of every step kernel.
+// The relaxation term of Eq. (SEC-VON-11) at a node, in the form update()
+// takes it.  FP32 (increment form): r_i = omega (f^eq_i - f_i), moment-exact
+// in the modes that ask for it.  FP64: r_i = omega f^eq_i.
 template <typename S, int TM, typename V = S>
 __device__ __forceinline__ void relaxation(const Model<S>& M, const V (&f)[9], V rho, V ux, V uy, V T,
-                                           V (&ofe)[9]) {
-    omega_equilibrium<S, V>(M, rho, ux, uy, T, ofe);
-    conserve<S, TM, V>(M, f, ofe);
+                                           V (&r)[9]) {
+    omega_equilibrium<S, V>(M, rho, ux, uy, T, r);
+    if constexpr (std::is_same<S, float>::value) {
+#pragma unroll
+        for (int i = 0; i < 9; ++i) r[i] = fma_(-M.omega, f[i], r[i]);
+        conserve_increment<S, TM, V>(M, r);
+    }
 }
 
-// Update of one population from its five-point star and omega f^eq
-// (Eq. SEC-VON-11 with the folded weights of Model::w).
+// Update of one population from its five-point star and the relaxation term
+// r (Eq. SEC-VON-11 with the folded weights of Model).  FP32: the paper's
+// increment form, f' = c + (r + wi c + w1 e + w2 w + w3 n + w4 s): the
+// increment is small next to c, so its rounding errors are too, and a node
+// whose increment rounds away keeps its bits (a uniform state stays put
+// instead of drifting by the roundings of a full recomputation every step).
+// FP64: f' = w0 c + w1 e + w2 w + w3 n + w4 s + r.
 template <typename S, typename V = S>
-__device__ __forceinline__ V update(const Model<S>& M, int i, V ofe, V c, V e, V w, V n, V s) {
-    V acc = fma_(M.w[i][0], c, ofe);
-    acc = fma_(M.w[i][1], e, acc);
-    acc = fma_(M.w[i][2], w, acc);
-    acc = fma_(M.w[i][3], n, acc);
-    return fma_(M.w[i][4], s, acc);
+__device__ __forceinline__ V update(const Model<S>& M, int i, V r, V c, V e, V w, V n, V s) {
+    if constexpr (std::is_same<S, float>::value) {
+        V acc = fma_(M.wi[i], c, r);
+        acc = fma_(M.w[i][1], e, acc);
+        acc = fma_(M.w[i][2], w, acc);
+        acc = fma_(M.w[i][3], n, acc);
+        acc = fma_(M.w[i][4], s, acc);
+        return add_(c, acc);
+    } else {
+        V acc = fma_(M.w[i][0], c, r);
+        acc = fma_(M.w[i][1], e, acc);
+        acc = fma_(M.w[i][2], w, acc);
+        acc = fma_(M.w[i][3], n, acc);
+        return fma_(M.w[i][4], s, acc);
+    }
 }
 
 // ---------------------------------------------------------- ghost layer
@@ -526,7 +546,10 @@ __device__ __forceinline__ void report(unsigned* status, unsigned bits) {
 // recovery (69.3 against 67.4 GLUPS) and the plain FP32 mode (78.9 / 77.8),
 // scalar for the FP32 total-energy mode (76.8 / 68.9, where the packed form
 // runs out of registers).  LBM_PAIR_PACKED: 0 scalar in every mode, 1 per
-// mode as measured, 2 packed in every mode.
+// mode as measured, 2 packed in every mode.  (The batch kernel, whose model
+// constants sit in shared memory rather than in the kernel parameters, is
+// faster with the scalar form in every mode: 58.0 against 54.8 GLUPS on 256
+// tubes with double-float T.)
 #ifndef LBM_PAIR_PACKED
 #define LBM_PAIR_PACKED 1
 #endif
@@ -535,11 +558,11 @@ constexpr bool packed_pair() {
     return LBM_PAIR_PACKED == 2 || (LBM_PAIR_PACKED == 1 && (TM == T_DF || TM == T_INT32));
 }
 
-template <int TM>
+template <int TM, bool kPacked = packed_pair<TM>()>
 __device__ __forceinline__ unsigned pair_update(const Model<float>& M, const float* b, int P, int dn, int ds,
                                                 int nvalid, float2 (&o)[9]) {
     unsigned bits = 0;
-    if constexpr (packed_pair<TM>()) {
+    if constexpr (kPacked) {
         F2 C[9];
 #pragma unroll
         for (int i = 0; i < 9; ++i) C[i].v = *reinterpret_cast<const unsigned long long*>(b + i * P);

@@ -264,3 +264,23 @@ def test_paper_dmr_constants_go_nonphysical_but_the_vetted_set_does_not():
     good = W.dmr_paper(t_end=0.04)
     f = oracle.init(good, *W.initial_fields(good))
     assert oracle.run(good, f, good.steps) == 0
+
+
+def test_fp32_storage_run_is_the_fp64_step_rounded_to_fp32():
+    """The FP32-storage run (the error floor of any implementation that
+    stores f in FP32): from a state that is already FP32-exact, with sides
+    whose ghosts are copies of interior values (periodic, outflow), one step
+    is exactly the plain FP64 step with every value rounded to FP32."""
+    rng = np.random.Generator(np.random.PCG64(11))
+    sides = (Side("periodic"), Side("periodic"), Side("outflow"), Side("outflow"))
+    p = W.uniform(23, 9, (1.0, 0.0, 0.0, 1.0), dx=0.01, alpha=0.1, sides=sides, steps=1)
+    fields = (1.0 + 0.3 * rng.random((9, 23)), 0.4 * rng.standard_normal((9, 23)),
+              0.4 * rng.standard_normal((9, 23)), 1.0 + 0.3 * rng.random((9, 23)))
+    f = oracle.init(p, *fields)
+    oracle.interior(f)[:] = oracle.interior(f).astype(np.float32).astype(np.float64)
+    got, want = f.copy(), f.copy()
+    assert oracle.run(p, got, 1, 0, f32_storage=True) == 0
+    assert oracle.run(p, want, 1, 0) == 0
+    gi, wi = oracle.interior(got), oracle.interior(want)
+    assert not np.array_equal(wi, wi.astype(np.float32))  # the plain step leaves FP32
+    assert np.array_equal(gi, wi.astype(np.float32).astype(np.float64))
