@@ -519,7 +519,8 @@ lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx
     } else {
         for (int k = 0; k < 2 && e == cudaSuccess; ++k) e = dev_malloc(&c->f[k], fbytes);
     }
-    if (e == cudaSuccess) e = dev_malloc((void**)&c->d_status, sizeof(unsigned));
+    // status word, a spare, and the tile kernel's two scheduling counters
+    if (e == cudaSuccess) e = dev_malloc((void**)&c->d_status, 4 * sizeof(unsigned));
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_status, sizeof(unsigned));
     const int np = c->prec == LBM_FP64 ? conservation_partials(c->gd) : conservation_partials(c->gf);
     if (e == cudaSuccess) e = dev_malloc((void**)&c->d_partials, sizeof(double) * 4 * np);
@@ -527,7 +528,7 @@ lbm_status lbm_create(int nx, int ny, double b, double tau, double dt, double dx
     if (e == cudaSuccess) e = cudaMallocHost((void**)&c->h_sums, sizeof(double) * 4);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[0], 0, fbytes, c->stream);
     if (e == cudaSuccess) e = cudaMemsetAsync(c->f[1], 0, fbytes, c->stream);
-    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(unsigned), c->stream);
+    if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, 4 * sizeof(unsigned), c->stream);
     if (e != cudaSuccess) {
         lbm_status r = cuda_fail(nullptr, e, "allocating context buffers");
         lbm_destroy(c);

@@ -284,6 +284,24 @@ __device__ __forceinline__ void moments(const V (&f)[9], const Model<S>& M, V& r
             const V qa = add_(add_(add_(q[0], q[1]), add_(q[2], q[3])), add_(add_(q[4], q[5]), add_(q[6], q[7])));
             const V ea = add_(add_(add_(e01, e23), add_(e45, e67)), add_(add_(e03, e47), add_(e07, e08)));
             e = add_(hi, add_(add_(qa, q[8]), ea));
+#elif LBM_TDF_TREE == 2
+            // two sequential TwoSum chains (terms 0..4 and 5..8) merged by one
+            // more TwoSum: half the dependency depth of one chain
+            V ha{}, la{}, hb{}, lb{};
+#pragma unroll
+            for (int i = 0; i < 9; ++i) {
+                V& hi = i < 5 ? ha : hb;
+                V& lo = i < 5 ? la : lb;
+                const V p = mul_(f[i], w[i]);
+                const V q = fma_(f[i], w[i], neg_(p));
+                const V s = add_(hi, p);
+                const V bb = sub_(s, hi);
+                lo = add_(lo, add_(add_(sub_(hi, sub_(s, bb)), sub_(p, bb)), q));
+                hi = s;
+            }
+            V hi, eh;
+            two_sum(ha, hb, hi, eh);
+            e = add_(hi, add_(add_(la, lb), eh));
 #else
             // sequentially: TwoSum (Knuth) of each p_i into hi, errors in lo
             V hi{}, lo{};  // +0 in every lane
@@ -553,27 +571,54 @@ __device__ __forceinline__ void report(unsigned* status, unsigned bits) {
 #ifndef LBM_PAIR_PACKED
 #define LBM_PAIR_PACKED 1
 #endif
+// A pair from shared memory, read again each time (not kept in a register).
+__device__ __forceinline__ F2 lds_pair(const float* p) {
+    F2 r;
+    asm volatile("ld.shared.b64 %0, [%1];"
+                 : "=l"(r.v)
+                 : "r"(static_cast<unsigned>(__cvta_generic_to_shared(p))));
+    return r;
+}
+
 template <int TM>
 constexpr bool packed_pair() {
     return LBM_PAIR_PACKED == 2 || (LBM_PAIR_PACKED == 1 && (TM == T_DF || TM == T_INT32));
 }
 
-template <int TM, bool kPacked = packed_pair<TM>()>
+// kReload (packed form): the centre pairs are read from shared memory again
+// in each phase (moments, relaxation, update) instead of being kept in
+// registers across all three, which lowers the register peak by 18 (so that
+// more CTAs fit on an SM) for 18 more shared-memory loads.
+template <int TM, bool kPacked = packed_pair<TM>(), bool kReload = false>
 __device__ __forceinline__ unsigned pair_update(const Model<float>& M, const float* b, int P, int dn, int ds,
                                                 int nvalid, float2 (&o)[9]) {
     unsigned bits = 0;
     if constexpr (kPacked) {
-        F2 C[9];
+        auto centre = [&](F2 (&C)[9]) {
 #pragma unroll
-        for (int i = 0; i < 9; ++i) C[i].v = *reinterpret_cast<const unsigned long long*>(b + i * P);
+            for (int i = 0; i < 9; ++i) {
+                if constexpr (kReload)
+                    C[i] = lds_pair(b + i * P);
+                else
+                    C[i].v = *reinterpret_cast<const unsigned long long*>(b + i * P);
+            }
+        };
         F2 acc[9];
         {
             F2 rho, ux, uy, T;
-            moments<float, TM, F2>(C, M, rho, ux, uy, T);
+            {
+                F2 C[9];
+                centre(C);
+                moments<float, TM, F2>(C, M, rho, ux, uy, T);
+            }
             bits |= health(lane0(rho), lane0(ux), lane0(uy), lane0(T));
             if (nvalid == 2) bits |= health(lane1(rho), lane1(ux), lane1(uy), lane1(T));
+            F2 C[9];
+            centre(C);
             relaxation<float, TM, F2>(M, C, rho, ux, uy, T, acc);
         }
+        F2 C[9];
+        centre(C);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             const float* bp = b + i * P;

@@ -68,6 +68,10 @@ cudaError_t launch_tile_copy(const CUtensorMap& tmap, float* fout, const Grid<fl
                              cudaStream_t st);
 
 // One step, level `level` in fin -> level + 1 in fout (ghosts included).
+// status: 4 words, zero-initialised by the owner: [0] the health bits,
+// [2] and [3] the tile kernel's scheduling counters (zero between launches;
+// the kernel leaves them so); launches that share a status buffer must not
+// overlap.
 template <typename S, int TM>
 cudaError_t launch_step(const S* fin, S* fout, const Model<S>& M, const Grid<S>& G,
                         long long level, unsigned* status, cudaStream_t st, const StepConfig& cfg);

@@ -76,4 +76,13 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const void* tmap, int x, 
         : "memory");
 }
 
+// Programmatic dependent launch (sm_90+): wait until the grids this one
+// depends on have completed and their memory is visible (returns at once
+// for a grid not launched as a dependent), and let the next dependent grid
+// be scheduled.
+__device__ __forceinline__ void grid_dependency_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dependents_launch() {
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 }  // namespace lbm

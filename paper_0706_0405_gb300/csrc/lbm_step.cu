@@ -57,41 +57,74 @@ cudaError_t launch_vec(const float* fin, float* fout, const Model<float>& M, con
 }
 
 // ------------------------------------------------------ FP32 TMA tile kernel
-// Persistent CTAs of 32 x LBM_TILE_Y threads (default 32 x 4, six CTAs per
-// SM) walk 64 x LBM_TILE_Y-node tiles.  For each tile one thread issues a
-// single tiled tensor copy of the 72 x (LBM_TILE_Y + 2) x 9 box (4 extra
-// columns on each side for 16-byte alignment, one extra row above and below,
-// all nine planes) into one of two shared-memory stages; the next tile's box
-// is in flight while the current one is computed.  Each thread
-// updates two x-adjacent nodes: it reads their values and those of the rows
-// above and below as 8-byte pairs from shared memory, the outer x neighbours
-// as single floats, and writes 8-byte pairs (no global loads, no per-load
-// 64-bit address arithmetic).  Waits are bounded: on give-up the CTA raises
-// ST_TIMEOUT, drains its copies in flight and returns.
+// Persistent CTAs of 32 x LBM_TILE_Y threads (default 32 x 4) walk
+// 64 x LBM_TILE_Y-node tiles.  For each tile one thread issues a single tiled
+// tensor copy of the 72 x (LBM_TILE_Y + 2) x 9 box (4 extra columns on each
+// side for 16-byte alignment, one extra row above and below, all nine
+// planes) into one of two shared-memory stages; the next tile's box is in
+// flight while the current one is computed.  Each thread updates two
+// x-adjacent nodes (pair_update): it reads their values and those of the
+// rows above and below as 8-byte pairs from shared memory, the outer x
+// neighbours as single floats, and writes 8-byte pairs.
+// CTA j walks tiles j, j + grid, j + 2 grid, ... (static), or claims its
+// next tile at run time from a counter in global memory (one atomic per
+// tile, one tile ahead of its copy), so that every CTA stays busy until the
+// grid runs out of tiles whatever the ratio of tiles to CTAs; the last CTA
+// to leave then resets the counter for the next launch.  Waits are bounded:
+// on give-up the CTA raises ST_TIMEOUT, lets its copies in flight land and
+// leaves.
 #ifndef LBM_TILE_Y
 #define LBM_TILE_Y 4
 #endif
 constexpr int kTileX = 64, kTileY = LBM_TILE_Y;
 constexpr int kTileThreads = (kTileX / 2) * kTileY;
-
 constexpr int kBoxX = kTileX + 8, kBoxY = kTileY + 2;
 constexpr int kBoxFloats = kBoxX * kBoxY * 9;
 constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages start on 128-byte boundaries
 
 // Shared-memory stages per CTA (boxes in flight + the one being computed) and
-// the resident CTAs per SM the register budget is set for.
+// the resident CTAs per SM the register budget is set for: 6 (80 registers)
+// in every mode but the double-float one, whose packed update with the
+// centre pairs re-read from shared memory fits 72 registers and so 7 CTAs
+// (measured on the 4096 x 1024 double Mach reflection: double-float T 69.6
+// -> 70.9 GLUPS from 6 to 7 CTAs; FP32 total-energy T 78.1 -> 74.9).
 #ifndef LBM_TILE_STAGES
 #define LBM_TILE_STAGES 2
 #endif
 #ifndef LBM_TILE_MIN_BLOCKS
 #define LBM_TILE_MIN_BLOCKS 6
 #endif
+#ifndef LBM_TILE_MIN_BLOCKS_DF
+#define LBM_TILE_MIN_BLOCKS_DF 7
+#endif
+template <int TM>
+constexpr int tile_min_blocks() {
+    return TM == T_DF ? LBM_TILE_MIN_BLOCKS_DF : LBM_TILE_MIN_BLOCKS;
+}
+// Tiles claimed at run time (see below) where the grid's CTAs do not divide
+// the tiles evenly: with 7 CTAs per SM on the 4096 x 1024 grid (16384 tiles,
+// 1064 CTAs) a static walk gives 16 tiles to some CTAs and 15 to others
+// (70.9 -> 72.4 GLUPS with run-time claims); with 6 (912 CTAs, 17.96 each)
+// the static walk is already even and the claims only cost (78.1 -> 75.7).
+template <int TM>
+constexpr bool dynamic_tiles() {
+    return tile_min_blocks<TM>() != LBM_TILE_MIN_BLOCKS;
+}
 constexpr int kStages = LBM_TILE_STAGES;
 static_assert(kStages >= 2 && kStages <= 8, "2 to 8 stages");
 constexpr size_t kTileSmem = 128 + sizeof(float) * kStages * kStageFloats + kStages * sizeof(uint64_t);
+constexpr int kNoTile = 0x7fffffff;
+// 1: each step is launched as a programmatic dependent of the previous
+// launch on the stream (its CTAs are scheduled while the previous grid
+// drains, and wait for that grid's completion before touching memory).
+#ifndef LBM_TILE_PDL
+#define LBM_TILE_PDL 1
+#endif
 
+// status[0]: health bits; status[2], status[3]: the tile counter and the
+// count of CTAs that have left (both zero between launches).
 template <int TM>
-__global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
+__global__ void __launch_bounds__(kTileThreads, tile_min_blocks<TM>())
     k_step_tile(const __grid_constant__ CUtensorMap tmap, float* __restrict__ fout, const Model<float> M,
                 const Grid<float> G, long long level, unsigned* status, int tiles_x, int ntiles) {
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -100,56 +133,78 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
     float* box = reinterpret_cast<float*>(smem);
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(float) * kStages * kStageFloats);
     __shared__ int abort_flag;
+    __shared__ int tile_of[kStages];  // tile held in each stage (kNoTile: none)
+    unsigned* const counter = status + 2;
+    unsigned* const left = status + 3;
     const int tid = threadIdx.x, tx = tid % (kTileX / 2), ty = tid / (kTileX / 2);
-    if (tid == 0) {
-        for (int j = 0; j < kStages; ++j) mbar_init(&bar[j], 1);
-        fence_mbar_init();
-        abort_flag = 0;
-    }
-    __syncthreads();
+    // Launched as a programmatic dependent of the previous step: nothing of
+    // the two levels (the previous step writes this step's input and reads
+    // its output buffer) or of the counters is touched before the previous
+    // grid has completed; the next step may be scheduled from here on, its
+    // CTAs taking SM slots as this grid's CTAs leave.
+    grid_dependency_wait();
+    grid_dependents_launch();
     auto issue = [&](int tile, int stage) {
         const int x0 = (tile % tiles_x) * kTileX, y0 = (tile / tiles_x) * kTileY;
         mbar_arrive_expect_tx(&bar[stage], (uint32_t)(sizeof(float) * kBoxFloats));
         // array column x0 is interior column x0 - 4; array row y0 is interior row y0 - 1
         tma_load_3d(box + stage * kStageFloats, &tmap, x0, 0, y0, &bar[stage]);
     };
+    constexpr bool kDyn = dynamic_tiles<TM>();
+    // the tile of this CTA's local tile k: static walk, or (run-time claims)
+    // the one held in k's stage
+    auto tile_at = [&](int k) {
+        if constexpr (kDyn) {
+            return tile_of[k % kStages];
+        } else {
+            const int t = blockIdx.x + k * gridDim.x;
+            return t < ntiles ? t : kNoTile;
+        }
+    };
+    // take the tile of local tile k into its stage and start its copy (thread 0)
+    auto claim = [&](int k) {
+        const int stage = k % kStages;
+        if constexpr (!kDyn) {
+            const int t = tile_at(k);
+            if (t != kNoTile) issue(t, stage);
+            return;
+        }
+        const unsigned t = atomicAdd(counter, 1u);
+        if (t < (unsigned)ntiles) {
+            tile_of[stage] = (int)t;
+            issue((int)t, stage);
+        } else {
+            tile_of[stage] = kNoTile;
+        }
+    };
     // local tile k of this CTA lives in stage k % kStages; its phase parity
     // is (k / kStages) & 1
     auto wait = [&](int k) {
         return mbar_wait_bounded(&bar[k % kStages], (uint32_t)((k / kStages) & 1), kWaitLimit);
     };
-    int issued = -1, waited = -1;  // local tile indices (same in every thread)
-    for (int j = 0; j < kStages - 1; ++j) {  // fill all stages but one
-        const int t = blockIdx.x + j * gridDim.x;
-        if (t >= ntiles) break;
-        if (tid == 0) issue(t, j);
-        issued = j;
+    if (tid == 0) {
+        for (int j = 0; j < kStages; ++j) mbar_init(&bar[j], 1);
+        fence_mbar_init();
+        abort_flag = 0;
+        for (int j = 0; j < kStages; ++j) tile_of[j] = kNoTile;
+        for (int j = 0; j < kStages - 1; ++j) claim(j);  // fill all stages but one
     }
+    __syncthreads();
     const size_t pl = (size_t)G.plane;
     // the box in shared memory is [row][population][column], like the level
     constexpr int P = kBoxX, R = 9 * kBoxX;  // population and row strides in the box
     unsigned bits = 0;
-    for (int k = 0;; ++k) {
-        const int t = blockIdx.x + k * gridDim.x;
-        if (t >= ntiles) break;
+    int k = 0;
+    for (;; ++k) {
         // one thread waits for tile k (the others sleep in the barrier rather
         // than spin); the barrier then also says every thread is done with
         // tile k - 1, whose stage the next copy overwrites
-        if (tid == 0 && !wait(k)) abort_flag = 1;
+        if (tid == 0 && tile_at(k) != kNoTile && !wait(k)) abort_flag = 1;
         __syncthreads();
-        if (abort_flag) {
-            for (int j = waited + 1; j <= issued; ++j) wait(j);
-            if (tid == 0) atomicOr(status, ST_TIMEOUT);
-            return;
-        }
-        waited = k;
-        {  // the stage of tile k - 1 now takes tile k + kStages - 1
-            const int kn = k + kStages - 1, tn = blockIdx.x + kn * gridDim.x;
-            if (tn < ntiles) {
-                if (tid == 0) issue(tn, kn % kStages);
-                issued = kn;
-            }
-        }
+        const int t = tile_at(k);
+        if (abort_flag || t == kNoTile) break;
+        // the stage of tile k - 1 now takes the next tile
+        if (tid == 0) claim(k + kStages - 1);
         const int ix0 = (t % tiles_x) * kTileX + 2 * tx, iy = (t / tiles_x) * kTileY + ty;
         if (ix0 >= G.nx || iy >= G.ny) continue;
         const int nvalid = min(2, G.nx - ix0);
@@ -158,7 +213,7 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
         const size_t c0 = cell(G, ix0, iy);  // 8-byte aligned: ix0 + PADX is even
         float* out = fout + c0;
         float2 o[9];
-        bits |= pair_update<TM>(M, b, P, R, -R, nvalid, o);
+        bits |= pair_update<TM, packed_pair<TM>(), TM == T_DF>(M, b, P, R, -R, nvalid, o);
 #pragma unroll
         for (int i = 0; i < 9; ++i) {
             if (nvalid == 2)
@@ -180,6 +235,26 @@ __global__ void __launch_bounds__(kTileThreads, LBM_TILE_MIN_BLOCKS)
         }
     }
     report(status, bits);
+    if (tid == 0) {
+        if (abort_flag) {
+            // let the copies in flight land before the CTA's shared memory
+            // goes away: tile k (whose wait gave up) and the tiles claimed
+            // after it were issued but not waited for
+            for (int j = 0; j < kStages - 1; ++j)
+                if (tile_at(k + j) != kNoTile) wait(k + j);
+            atomicOr(status, ST_TIMEOUT);
+        }
+        if constexpr (kDyn) {
+            // every claim of this CTA is made; the last CTA out resets the
+            // counters for the next launch
+            __threadfence();
+            if (atomicAdd(left, 1u) == gridDim.x - 1) {
+                *counter = 0;
+                *left = 0;
+                __threadfence();
+            }
+        }
+    }
 }
 
 // Data-movement twin of k_step_tile for lbm_probe_tile_copy: the same tile
@@ -278,8 +353,17 @@ cudaError_t launch_tile(const CUtensorMap& tmap, float* fout, const Model<float>
     int grid = grid_hint;
     if (grid <= 0) grid = full_wave<k_step_tile<TM>>(kTileThreads, smem);
     if (grid > ntiles) grid = ntiles;
-    kern<<<grid, kTileThreads, smem, st>>>(tmap, fout, M, G, level, status, tiles_x, ntiles);
-    return cudaGetLastError();
+    cudaLaunchConfig_t lc{};
+    lc.gridDim = dim3(grid);
+    lc.blockDim = dim3(kTileThreads);
+    lc.dynamicSmemBytes = smem;
+    lc.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    at[0].val.programmaticStreamSerializationAllowed = LBM_TILE_PDL;
+    lc.attrs = at;
+    lc.numAttrs = 1;
+    return cudaLaunchKernelEx(&lc, kern, tmap, fout, M, G, level, status, tiles_x, ntiles);
 }
 
 // ------------------------------------------------------ FP32 ring kernel

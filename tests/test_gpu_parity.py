@@ -301,14 +301,17 @@ def test_step_before_init_is_a_state_error():
 
 # ---------------------------------------------------------- launch shapes
 
-SHAPES = [(0, 0, 0, 0), (3, 0, 0, 0), (3, 0, 0, 5), (2, 4, 0, 0), (2, 2, 0, 0), (1, 256, 4, 0),
-          (1, 256, 6, 0), (1, 128, 4, 0), (1, 256, 4, 7), (1, 128, 4, 1)]
+SHAPES = [(0, 0, 0, 0), (3, 0, 0, 0), (3, 0, 0, 5), (3, 0, 0, 1), (3, 0, 0, 13), (2, 4, 0, 0), (2, 2, 0, 0),
+          (1, 256, 4, 0), (1, 256, 6, 0), (1, 128, 4, 0), (1, 256, 4, 7), (1, 128, 4, 1)]
 
 
 @pytest.mark.parametrize("prec", FP32_MODES)
 @pytest.mark.parametrize("ny", [64, 37])
 def test_every_launch_shape_gives_the_same_bits(prec, ny):
-    """The thread-per-node kernel, the TMA tile kernel (full wave and 5 CTAs),
+    """The thread-per-node kernel, the TMA tile kernel (full wave, 1, 5 and 13
+    CTAs; in the double-float mode the CTAs claim their tiles at run time,
+    25 launches in a row, so a claim counter not reset between launches
+    would show),
     the vectorised kernel (2 and 4 nodes per thread) and every shape of the
     strip-marching ring kernel (including a grid of 1 and 7 CTAs), on a grid
     whose width is not a multiple of any tile, vector or strip width, do the
