@@ -135,17 +135,17 @@ def hbm_peak():
         return 6800.0, "fallback"
 
 
-def recorded_traffic(kernel: str):
+def recorded_traffic(kernel: str, precision: str):
     """DRAM bytes per launch from profiles/dram_traffic.txt if that capture was
     taken on the kernel's current sources (same hash of the files that define
-    it), else None."""
+    it) in the same precision mode, else None."""
     from paper_0706_0405_gb300 import build as B
     src = B.kernel_hash(kernel)
     try:
         with open(os.path.join(ROOT, "profiles", "dram_traffic.txt")) as fh:
             for line in fh:
                 kv = dict(t.split("=", 1) for t in line.split() if "=" in t)
-                if kv.get("kernel") == kernel and kv.get("src") == src:
+                if kv.get("kernel") == kernel and kv.get("src") == src and kv.get("precision") == precision:
                     return float(kv["bytes_per_launch"])
     except OSError:
         pass
@@ -257,7 +257,7 @@ def run_ours(args, world, dist):
                    "l2": "inputs larger than L2 (152 MB per level, two levels)",
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
-                     "frac": round(achieved / peak, 4), "traffic": recorded_traffic(kname),
+                     "frac": round(achieved / peak, 4), "traffic": recorded_traffic(kname, args.precision),
                      "peak_kind": peak_kind, "algorithmic_bytes_per_node": bpn,
                      "kernel": kname, "kernel_ms": round(kernel_ms, 5),
                      "kernel_ms_from": "timed region / launches (all launches in it are this kernel)",
