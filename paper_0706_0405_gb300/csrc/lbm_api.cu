@@ -42,6 +42,20 @@ bool is_device_ptr(const void* p) {
     return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
 }
 
+// The device's address of page-locked host memory (cudaMallocHost,
+// cudaHostRegister, torch pin_memory), or nullptr for any other pointer.  On
+// a Grace-Blackwell node the GPU reads and writes such memory over the
+// coherent CPU-GPU link, so a kernel can stream it directly instead of
+// through a staging copy.
+void* pinned_alias(const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return nullptr;
+    }
+    return a.type == cudaMemoryTypeHost ? a.devicePointer : nullptr;
+}
+
 // Velocity signs of Eq. (e14) with the diagonals read as c2 (cos, sin).
 constexpr int SGX[9] = {0, -1, 0, 1, 0, -1, 1, 1, -1};
 constexpr int SGY[9] = {0, 0, -1, 0, 1, -1, -1, 1, 1};
@@ -288,6 +302,10 @@ lbm_status device_view(lbm_ctx* c, const void* p, size_t bytes, size_t offset, c
     }
     if (is_device_ptr(p)) {
         *out = p;
+        return LBM_OK;
+    }
+    if (const void* alias = pinned_alias(p)) {  // read in place by the kernel
+        *out = alias;
         return LBM_OK;
     }
     char* dst = static_cast<char*>(c->d_stage) + offset;
@@ -629,13 +647,24 @@ lbm_status lbm_moments(lbm_ctx* c, void* rho, void* ux, void* uy, void* T) {
     const size_t fb = nodes(c) * c->esize;
     void* out[4] = {rho, ux, uy, T};
     void* dev[4];
-    bool host_any = false;
+    bool host_any = false, stage_any = false;
     for (int k = 0; k < 4; ++k) {
-        if (out[k] && !is_device_ptr(out[k])) host_any = true;
+        dev[k] = nullptr;
+        if (!out[k]) continue;
+        if (is_device_ptr(out[k])) {
+            dev[k] = out[k];
+            continue;
+        }
+        host_any = true;
+        dev[k] = pinned_alias(out[k]);  // page-locked: the kernel writes it in place
+        if (!dev[k]) stage_any = true;
     }
-    if (host_any && (s = ensure_stage(c, 9 * fb)) != LBM_OK) return s;
-    for (int k = 0; k < 4; ++k)
-        dev[k] = !out[k] ? nullptr : is_device_ptr(out[k]) ? out[k] : static_cast<char*>(c->d_stage) + k * fb;
+    if (stage_any && (s = ensure_stage(c, 9 * fb)) != LBM_OK) return s;
+    void* aliased[4];
+    for (int k = 0; k < 4; ++k) {
+        aliased[k] = dev[k];
+        if (out[k] && !dev[k]) dev[k] = static_cast<char*>(c->d_stage) + k * fb;
+    }
     cudaError_t e = dispatch(c, [&](auto tag, auto tm) {
         using S = decltype(tag);
         constexpr int TM = decltype(tm)::value;
@@ -644,7 +673,7 @@ lbm_status lbm_moments(lbm_ctx* c, void* rho, void* ux, void* uy, void* T) {
     });
     if (e != cudaSuccess) return cuda_fail(c, e, "lbm_moments");
     for (int k = 0; k < 4; ++k)
-        if (out[k] && dev[k] != out[k])
+        if (out[k] && !aliased[k])
             LBM_CUDA(c, cudaMemcpyAsync(out[k], dev[k], fb, cudaMemcpyDeviceToHost, c->stream), "copying moments out");
     if (host_any) return read_status(c);
     return LBM_OK;

@@ -101,6 +101,9 @@ template <int TM>
 constexpr int tile_min_blocks() {
     return TM == T_DF ? LBM_TILE_MIN_BLOCKS_DF : LBM_TILE_MIN_BLOCKS;
 }
+#ifndef LBM_TILE_DYNAMIC
+#define LBM_TILE_DYNAMIC 1  // 0: static walk everywhere, 1: as measured below, 2: claims everywhere
+#endif
 // Tiles claimed at run time (see below) where the grid's CTAs do not divide
 // the tiles evenly: with 7 CTAs per SM on the 4096 x 1024 grid (16384 tiles,
 // 1064 CTAs) a static walk gives 16 tiles to some CTAs and 15 to others
@@ -108,7 +111,7 @@ constexpr int tile_min_blocks() {
 // the static walk is already even and the claims only cost (78.1 -> 75.7).
 template <int TM>
 constexpr bool dynamic_tiles() {
-    return tile_min_blocks<TM>() != LBM_TILE_MIN_BLOCKS;
+    return LBM_TILE_DYNAMIC == 2 || (LBM_TILE_DYNAMIC == 1 && tile_min_blocks<TM>() != LBM_TILE_MIN_BLOCKS);
 }
 constexpr int kStages = LBM_TILE_STAGES;
 static_assert(kStages >= 2 && kStages <= 8, "2 to 8 stages");
