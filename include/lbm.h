@@ -317,8 +317,7 @@ lbm_status lbm_autotune(lbm_ctx* ctx, int steps, lbm_launch* best, double* ms, i
  *    runtime's primary context) looks up that array's device address in
  *    that context, with the device current, and keeps it under the
  *    context's unique ID; a non-primary context, or a new primary context
- *    after cudaDeviceReset, does its own look-up.  Make that first call
- *    before any stream capture.
+ *    after cudaDeviceReset, does its own look-up.
  *  - All calls share the array; calls that overlap on the GPU race and may
  *    return wrong totals.  Each call writes every value it reads, so a call
  *    never depends on an earlier call's contents.
