@@ -218,11 +218,13 @@ def run_ours(args, world, dist):
     peak, peak_kind = hbm_peak()
 
     lat = lbm.Lattice(p, args.precision)
-    lat.init(*fields).step(args.warmup)
-    lat.sync()
-    if dist:
-        dist.barrier()
+    # the sampler starts (and settles) before the warm-up steps, so that the
+    # timed steps follow the warm-up without an idle gap
     with ClockSampler(dev) as clocks:
+        lat.init(*fields).step(args.warmup)
+        lat.sync()
+        if dist:
+            dist.barrier()
         secs = timed_steps(lat, args.steps, stream)
     # every launch in the timed region is the step kernel (one per step), so
     # the region's event time over the launch count is its mean launch
