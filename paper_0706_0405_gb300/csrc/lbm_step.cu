@@ -73,10 +73,14 @@ cudaError_t launch_vec(const float* fin, float* fout, const Model<float>& M, con
 // to leave then resets the counter for the next launch.  Waits are bounded:
 // on give-up the CTA raises ST_TIMEOUT, lets its copies in flight land and
 // leaves.
+#ifndef LBM_TILE_X
+#define LBM_TILE_X 64
+#endif
 #ifndef LBM_TILE_Y
 #define LBM_TILE_Y 4
 #endif
-constexpr int kTileX = 64, kTileY = LBM_TILE_Y;
+constexpr int kTileX = LBM_TILE_X, kTileY = LBM_TILE_Y;
+static_assert(kTileX % 32 == 0, "tile width: a multiple of 32 columns");
 constexpr int kTileThreads = (kTileX / 2) * kTileY;
 constexpr int kBoxX = kTileX + 8, kBoxY = kTileY + 2;
 constexpr int kBoxFloats = kBoxX * kBoxY * 9;
