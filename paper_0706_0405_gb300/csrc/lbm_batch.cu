@@ -168,6 +168,7 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
     __shared__ Model<float> sM;
     __shared__ Grid<float> sG;
     __shared__ int abort_flag;
+    __shared__ int4 stage_T[2];  // the tile entry of the box in each stage
     extern __shared__ __align__(128) unsigned char smem_raw[];
     unsigned char* smem = smem_raw + ((128 - (smem_u32(smem_raw) & 127)) & 127);
     float* box0 = reinterpret_cast<float*>(smem);
@@ -203,6 +204,7 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
     // phase parity (k >> 1) & 1
     auto issue = [&](int t, int k, int par) {
         const int4 T = tiles[t];
+        stage_T[k & 1] = T;  // read by every thread after the barrier of tile k
         const BatchProb& Q = probs[T.x];
         mbar_arrive_expect_tx(&bar[k & 1], Q.box_bytes);
         // array column T.y (interior column T.y - 4), array row T.z (interior row T.z - 1);
@@ -211,6 +213,10 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
     };
     auto wait = [&](int k) { return mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), kBatchWaitLimit); };
     int k = 0, issued = -1, waited = -1;
+    // the problem whose constants are in shared memory (kept across steps:
+    // a CTA's first tile of a step mostly has the last one's problem)
+    int cur = -1;
+    bool wrap = false;  // the current problem wraps in y inside its tiles
     for (int s = 0; s < nsteps; ++s) {
         const long long level = level0 + s;
         const int par = (int)(level & 1);
@@ -220,8 +226,6 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
             if (tid == 0) issue(t0, k, par);
             issued = k;
         }
-        int cur = -1;
-        bool wrap = false;  // the current problem wraps in y inside its tiles
         // y ghost rows of such problems are written on the launch's last step only
         const bool last = s == nsteps - 1;
         for (int t = t0; t < t1; t += stride, ++k) {
@@ -239,7 +243,7 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
                 if (tid == 0) issue(t + stride, k + 1, par);
                 issued = k + 1;
             }
-            const int4 T = tiles[t];
+            const int4 T = stage_T[k & 1];
             const BatchProb& P = probs[T.x];
             if (T.x != cur) {
                 copy_words(reinterpret_cast<float*>(&sM), reinterpret_cast<const float*>(&P.M),
