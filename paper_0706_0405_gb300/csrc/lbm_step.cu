@@ -127,6 +127,15 @@ constexpr int kNoTile = 0x7fffffff;
 #ifndef LBM_TILE_PDL
 #define LBM_TILE_PDL 1
 #endif
+// Run-time claims one tile ahead of the copies, the claim's result held in
+// a register of thread 0 (1: 75.2 -> 76.2 GLUPS over 400 steps in the
+// double-float mode), or each tile claimed just before its copy (0).  (Held
+// in shared memory instead, the claim stalls warp 0 right after the copy:
+// 73.3.)
+#ifndef LBM_TILE_CLAIM_AHEAD
+#define LBM_TILE_CLAIM_AHEAD 1
+#endif
+constexpr bool kClaimAhead = LBM_TILE_CLAIM_AHEAD != 0;
 
 // status[0]: health bits; status[2], status[3]: the tile counter and the
 // count of CTAs that have left (both zero between launches).
@@ -141,6 +150,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<TM>())
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem + sizeof(float) * kStages * kStageFloats);
     __shared__ int abort_flag;
     __shared__ int tile_of[kStages];  // tile held in each stage (kNoTile: none)
+    unsigned ahead = 0;  // run-time claims (thread 0): claimed, copy not yet issued
     unsigned* const counter = status + 2;
     unsigned* const left = status + 3;
     const int tid = threadIdx.x, tx = tid % (kTileX / 2), ty = tid / (kTileX / 2);
@@ -176,6 +186,21 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<TM>())
             if (t != kNoTile) issue(t, stage);
             return;
         }
+        if constexpr (kClaimAhead) {
+            // the tile was claimed one round earlier: its copy starts now; the
+            // next claim's atomic is issued after the copy, and its result is
+            // first needed a tile later, so its round trip overlaps the tile's
+            // arithmetic instead of delaying the copy
+            const unsigned t = ahead;
+            if (t < (unsigned)ntiles) {
+                tile_of[stage] = (int)t;
+                issue((int)t, stage);
+                ahead = atomicAdd(counter, 1u);
+            } else {
+                tile_of[stage] = kNoTile;
+            }
+            return;
+        }
         const unsigned t = atomicAdd(counter, 1u);
         if (t < (unsigned)ntiles) {
             tile_of[stage] = (int)t;
@@ -194,6 +219,7 @@ __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<TM>())
         fence_mbar_init();
         abort_flag = 0;
         for (int j = 0; j < kStages; ++j) tile_of[j] = kNoTile;
+        if constexpr (kDyn && kClaimAhead) ahead = atomicAdd(counter, 1u);
         for (int j = 0; j < kStages - 1; ++j) claim(j);  // fill all stages but one
     }
     __syncthreads();
