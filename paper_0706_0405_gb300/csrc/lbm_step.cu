@@ -135,11 +135,16 @@ constexpr int kNoTile = 0x7fffffff;
 #ifndef LBM_TILE_CLAIM_AHEAD
 #define LBM_TILE_CLAIM_AHEAD 1
 #endif
-constexpr bool kClaimAhead = LBM_TILE_CLAIM_AHEAD != 0;
+// Claims ahead are taken only where each CTA walks at least this many tiles
+// (chosen at launch): on a small grid a CTA that starts late would still take
+// its full share instead of leaving tiles to the CTAs that are free first
+// (the Mach-3 2048 x 256 tube, 1.9 tiles a CTA: 11.4 us a step with claims
+// ahead taken there too, 12.5).
+constexpr int kClaimAheadTiles = 8;
 
 // status[0]: health bits; status[2], status[3]: the tile counter and the
 // count of CTAs that have left (both zero between launches).
-template <int TM>
+template <int TM, bool kClaimAhead>
 __global__ void __launch_bounds__(kTileThreads, tile_min_blocks<TM>())
     k_step_tile(const __grid_constant__ CUtensorMap tmap, float* __restrict__ fout, const Model<float> M,
                 const Grid<float> G, long long level, unsigned* status, int tiles_x, int ntiles) {
@@ -378,14 +383,19 @@ template <int TM>
 cudaError_t launch_tile(const CUtensorMap& tmap, float* fout, const Model<float>& M, const Grid<float>& G,
                         long long level, unsigned* status, int grid_hint, cudaStream_t st) {
     constexpr size_t smem = kTileSmem;
-    auto kern = k_step_tile<TM>;
-    cudaError_t e = allow_smem<k_step_tile<TM>>(smem);
+    // both instances have the same launch bounds, so the same occupancy
+    cudaError_t e = allow_smem<k_step_tile<TM, false>>(smem);
+    if constexpr (dynamic_tiles<TM>())
+        if (e == cudaSuccess) e = allow_smem<k_step_tile<TM, true>>(smem);
     if (e != cudaSuccess) return e;
     const int tiles_x = (G.nx + kTileX - 1) / kTileX;
     const int ntiles = tiles_x * ((G.ny + kTileY - 1) / kTileY);
     int grid = grid_hint;
-    if (grid <= 0) grid = full_wave<k_step_tile<TM>>(kTileThreads, smem);
+    if (grid <= 0) grid = full_wave<k_step_tile<TM, false>>(kTileThreads, smem);
     if (grid > ntiles) grid = ntiles;
+    auto kern = k_step_tile<TM, false>;
+    if constexpr (dynamic_tiles<TM>())
+        if (LBM_TILE_CLAIM_AHEAD && ntiles >= kClaimAheadTiles * grid) kern = k_step_tile<TM, true>;
     cudaLaunchConfig_t lc{};
     lc.gridDim = dim3(grid);
     lc.blockDim = dim3(kTileThreads);
