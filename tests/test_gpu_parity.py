@@ -343,7 +343,8 @@ def test_every_launch_shape_gives_the_same_bits(prec, ny):
     """The thread-per-node kernel, the TMA tile kernel (full wave, 1, 5 and 13
     CTAs; in the double-float mode the CTAs claim their tiles at run time,
     25 launches in a row, so a claim counter not reset between launches
-    would show),
+    would show, and with 1 and 5 CTAs, 8 or more tiles each, they claim
+    ahead of the copies),
     the vectorised kernel (2 and 4 nodes per thread) and every shape of the
     strip-marching ring kernel (including a grid of 1 and 7 CTAs), on a grid
     whose width is not a multiple of any tile, vector or strip width, do the
