@@ -215,6 +215,10 @@ lbm_status lbm_batch_create(int nprob, const lbm_problem* probs, lbm_precision p
                 return bfail(nullptr, LBM_E_CUDA, "lbm_batch_create: tensor maps unavailable on this driver");
             }
     }
+    // each tile entry carries what issuing its copy needs from its problem:
+    // the box's bytes, and (top bit) whether the box starts one row lower
+    for (int4& t : tiles) t.w = (int)(hp[(size_t)t.x].box_bytes | (hp[(size_t)t.x].wrap ? 0x80000000u : 0u));
+    b->tiles = tiles;
     cudaError_t e = dev_malloc((void**)&b->d_probs, sizeof(BatchProb) * nprob);
     if (e == cudaSuccess) e = dev_malloc((void**)&b->d_tiles, sizeof(int4) * tiles.size());
     if (e == cudaSuccess && b->tb_ok) e = dev_malloc((void**)&b->d_segs, sizeof(int4) * segs.size());

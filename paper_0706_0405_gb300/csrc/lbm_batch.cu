@@ -205,11 +205,14 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
     auto issue = [&](int t, int k, int par) {
         const int4 T = tiles[t];
         stage_T[k & 1] = T;  // read by every thread after the barrier of tile k
-        const BatchProb& Q = probs[T.x];
-        mbar_arrive_expect_tx(&bar[k & 1], Q.box_bytes);
+        // T.w: the box's bytes, top bit set for a wrapping problem (no load of
+        // the problem's record before the copy: its tensor map is addressed)
+        const unsigned tw = (unsigned)T.w;
+        mbar_arrive_expect_tx(&bar[k & 1], tw & 0x7fffffffu);
         // array column T.y (interior column T.y - 4), array row T.z (interior row T.z - 1);
         // a wrapping problem's box starts one row lower, at its first interior row
-        tma_load_3d(box0 + (k & 1) * kStageFloats, &Q.tm[par], T.y, 0, T.z + Q.wrap, &bar[k & 1]);
+        tma_load_3d(box0 + (k & 1) * kStageFloats, &probs[T.x].tm[par], T.y, 0, T.z + (int)(tw >> 31),
+                    &bar[k & 1]);
     };
     auto wait = [&](int k) { return mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), kBatchWaitLimit); };
     int k = 0, issued = -1, waited = -1;
