@@ -10,6 +10,8 @@
 // flight while the current one is computed; every thread then updates one or
 // two nodes with the same per-node arithmetic as the single-grid kernels, so
 // each problem's levels are bit-identical to stepping it alone.
+#include <cstddef>
+
 #include "lbm_launch.h"
 #include "lbm_ptx.cuh"
 
@@ -160,13 +162,30 @@ constexpr int kBoxFloats = kBoxH * kBoxRow;
 constexpr int kStageFloats = (kBoxFloats + 31) / 32 * 32;  // stages on 128-byte boundaries
 constexpr size_t kBatchSmem = 128 + sizeof(float) * 2 * kStageFloats + 2 * sizeof(uint64_t);
 
+// A problem's constants (its Model and Grid, contiguous in BatchProb) travel
+// to shared memory as one bulk copy beside each box that starts a run of the
+// problem's tiles in a stage: kConstBytes from offset kConstOff of the record.
+constexpr size_t kConstOff = offsetof(BatchProb, M);
+constexpr size_t kGridInConst = offsetof(BatchProb, G) - kConstOff;
+constexpr size_t kConstBytes = (kGridInConst + sizeof(Grid<float>) + 15) / 16 * 16;
+static_assert(kConstOff % 16 == 0, "bulk copies start on 16-byte boundaries");
+static_assert(kConstOff + kConstBytes <= sizeof(BatchProb), "the copy stays inside the record");
+
+// CTAs per SM the register allocation must allow: 6 of 128 threads (at most
+// 80 registers a thread), 4 of 256 (64)
+template <int NPT>
+constexpr int batch_min_blocks() {
+    return NPT == 2 ? 6 : 4;
+}
+
 template <int TM, int NPT>
-__global__ void __launch_bounds__(batch_threads<NPT>())
+__global__ void __launch_bounds__(batch_threads<NPT>(), batch_min_blocks<NPT>())
     k_batch(const BatchProb* __restrict__ probs, const int4* __restrict__ tiles, int ntiles, int nsteps,
             long long* level_ptr, unsigned* bar_count, unsigned* bar_gen, unsigned* status,
             const int* __restrict__ nbr, unsigned long long* done, unsigned long long* epoch_ptr) {
-    __shared__ Model<float> sM;
-    __shared__ Grid<float> sG;
+    // each stage's problem constants (Model, then Grid at kGridInConst)
+    __shared__ __align__(16) unsigned char sConst[2][kConstBytes];
+    __shared__ int const_of[2];  // problem whose constants a stage holds (thread 0)
     __shared__ int abort_flag;
     __shared__ int4 stage_T[2];  // the tile entry of the box in each stage
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -179,6 +198,7 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
         mbar_init(&bar[1], 1);
         fence_mbar_init();
         abort_flag = 0;
+        const_of[0] = const_of[1] = -1;
     }
     __syncthreads();
     const long long level0 = *(volatile long long*)level_ptr;
@@ -208,18 +228,21 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
         // T.w: the box's bytes, top bit set for a wrapping problem (no load of
         // the problem's record before the copy: its tensor map is addressed)
         const unsigned tw = (unsigned)T.w;
-        mbar_arrive_expect_tx(&bar[k & 1], tw & 0x7fffffffu);
+        // the problem's constants come along unless the stage still holds them
+        const bool consts = const_of[k & 1] != T.x;
+        mbar_arrive_expect_tx(&bar[k & 1], (tw & 0x7fffffffu) + (consts ? (uint32_t)kConstBytes : 0u));
         // array column T.y (interior column T.y - 4), array row T.z (interior row T.z - 1);
         // a wrapping problem's box starts one row lower, at its first interior row
         tma_load_3d(box0 + (k & 1) * kStageFloats, &probs[T.x].tm[par], T.y, 0, T.z + (int)(tw >> 31),
                     &bar[k & 1]);
+        if (consts) {
+            bulk_g2s(sConst[k & 1], reinterpret_cast<const unsigned char*>(probs + T.x) + kConstOff,
+                     (uint32_t)kConstBytes, &bar[k & 1]);
+            const_of[k & 1] = T.x;
+        }
     };
     auto wait = [&](int k) { return mbar_wait_bounded(&bar[k & 1], (uint32_t)((k >> 1) & 1), kBatchWaitLimit); };
     int k = 0, issued = -1, waited = -1;
-    // the problem whose constants are in shared memory (kept across steps:
-    // a CTA's first tile of a step mostly has the last one's problem)
-    int cur = -1;
-    bool wrap = false;  // the current problem wraps in y inside its tiles
     for (int s = 0; s < nsteps; ++s) {
         const long long level = level0 + s;
         const int par = (int)(level & 1);
@@ -248,15 +271,10 @@ __global__ void __launch_bounds__(batch_threads<NPT>())
             }
             const int4 T = stage_T[k & 1];
             const BatchProb& P = probs[T.x];
-            if (T.x != cur) {
-                copy_words(reinterpret_cast<float*>(&sM), reinterpret_cast<const float*>(&P.M),
-                           (int)(sizeof(Model<float>) / sizeof(float)));
-                copy_words(reinterpret_cast<int*>(&sG), reinterpret_cast<const int*>(&P.G),
-                           (int)(sizeof(Grid<float>) / sizeof(int)));
-                cur = T.x;
-                __syncthreads();
-                wrap = wraps_in_tile(sG, kTileH);
-            }
+            const Model<float>& sM = *reinterpret_cast<const Model<float>*>(sConst[k & 1]);
+            const Grid<float>& sG = *reinterpret_cast<const Grid<float>*>(sConst[k & 1] + kGridInConst);
+            // the problem wraps in y inside its tiles
+            const bool wrap = (unsigned)T.w >> 31;
             if constexpr (NPT == 1) {
                 const int ix = T.y + cx, iy = T.z + r;
                 if (ix < sG.nx && iy < sG.ny) {
