@@ -32,7 +32,10 @@ __device__ long long g_wait_cycles = kBarrierCycles;
 constexpr uint32_t kBatchWaitLimit = 1u << 22;       // mbarrier probes before a wait gives up
 
 // Bounded grid-wide barrier for a cooperative launch.  Returns false (and
-// sets ST_TIMEOUT) if the barrier did not complete in time.  The stores of
+// sets ST_TIMEOUT) if the barrier did not complete in time or another CTA
+// has given up (ST_TIMEOUT already set); the decision is the CTA's, taken
+// by one thread and passed on by the CTA barrier, so all its threads leave
+// together.  The stores of
 // the step are ordered before the async-proxy reads (tensor copies) of the
 // next step on both sides: every thread fences after its stores, and the
 // thread that issues the copies fences after the barrier.
@@ -52,7 +55,7 @@ __device__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned* 
         } else {
             const long long t0 = clock64();
             while (*gen == g) {
-                if (clock64() - t0 > g_wait_cycles) {
+                if (clock64() - t0 > g_wait_cycles || (*(volatile unsigned*)status & ST_TIMEOUT)) {
                     atomicOr(status, ST_TIMEOUT);
                     ok = 0;
                     break;
@@ -75,7 +78,8 @@ __device__ bool grid_barrier(unsigned* count, volatile unsigned* gen, unsigned* 
 // the previous step.  That orders both the reads of the halo written by a
 // neighbour and the overwriting of the level a neighbour was still reading,
 // without making every CTA wait for the slowest one.  Same fences as the
-// grid barrier; the wait is bounded.
+// grid barrier; the wait is bounded, and gives up at once once another CTA
+// has given up (ST_TIMEOUT set), the CTA's threads leaving together.
 __device__ void publish_step(unsigned long long* done, unsigned long long value) {
     fence_proxy_async_global();
     __syncthreads();
@@ -89,13 +93,13 @@ __device__ bool wait_neighbours(const int* __restrict__ nbr, const unsigned long
                                 unsigned long long target, unsigned* status) {
     __shared__ int ok;
     if (threadIdx.x == 0) {
-        ok = 1;
+        ok = (*(volatile unsigned*)status & ST_TIMEOUT) ? 0 : 1;
         const long long t0 = clock64();
         for (int j = 0; j < kBatchMaxNbr && ok; ++j) {
             const int n = nbr[j];
             if (n < 0) break;
             while (*(volatile const unsigned long long*)(done + n) < target) {
-                if (clock64() - t0 > g_wait_cycles) {
+                if (clock64() - t0 > g_wait_cycles || (*(volatile unsigned*)status & ST_TIMEOUT)) {
                     atomicOr(status, ST_TIMEOUT);
                     ok = 0;
                     break;
@@ -246,7 +250,7 @@ __global__ void __launch_bounds__(batch_threads<NPT>(), batch_min_blocks<NPT>())
     for (int s = 0; s < nsteps; ++s) {
         const long long level = level0 + s;
         const int par = (int)(level & 1);
-        if (*(volatile unsigned*)status & ST_TIMEOUT) return;
+        // (a give-up elsewhere is seen in the waits below, by the CTA as a whole)
         if (s > 0 && my_nbr && !wait_neighbours(my_nbr, done, epoch0 + s, status)) return;
         if (t0 < t1) {
             if (tid == 0) issue(t0, k, par);
